@@ -1,0 +1,193 @@
+"""Geometry, collocation rows and manufactured data of the RFM discretisation.
+
+Follows Sec. 2.2 (subdomains Omega_i, affine map l_i(x) = (x - mu_i)/sigma_i,
+indicator partition of unity psi^a, tanh features phi_ij) and Sec. 5 (uniform
+collocation grids including endpoints, interface continuity rows C^0..C^{k-1},
+Eqs. con:1-3, and Dirichlet boundary rows, Eqs. bdy:1-3).  Row counts reproduce
+Sec. 3.2's formulas m = Q_I + Q_b + Q_c.
+
+Row order (a reading; the paper does not fix one):
+  1. interior rows: subdomain e (lexicographic, axis 0 slowest), field f,
+     grid point (lexicographic, axis 0 slowest);
+  2. interface rows: normal axis a = 0..d-1; left subdomain e (lexicographic)
+     with a right neighbour along a; field f; derivative order s = 0..k-1;
+     face point (remaining axes lexicographic);
+  3. boundary rows: axis a = 0..d-1; side lo then hi; subdomain e touching it
+     (lexicographic); field f; face point.
+Unknowns are ordered subdomain-major, then field, then feature.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+"""
+import math
+
+import numpy as np
+
+from . import philox
+
+
+class Problem:
+    def __init__(self, desc):
+        self.desc = desc
+        d = self.d = int(desc["dim"])
+        self.N = [int(x) for x in desc["nsub"][:d]]
+        self.G = int(np.prod(self.N))
+        self.M = int(desc["M"])
+        self.fields = int(desc["fields"])
+        self.W = self.fields * self.M
+        self.n = self.G * self.W
+        self.lo = [float(x) for x in desc["lo"][:d]]
+        self.hi = [float(x) for x in desc["hi"][:d]]
+        self.kind = int(desc["pde_kind"])
+        self.params = [float(p) for p in desc["pde_params"]]
+        self.cont = int(desc["cont_order"])
+        # breakpoints X_b[j] = lo + (hi - lo) * j / N, ends exact
+        self.X = []
+        for b in range(d):
+            xs = [self.lo[b] + ((self.hi[b] - self.lo[b]) * j) / self.N[b] for j in range(self.N[b] + 1)]
+            xs[0], xs[-1] = self.lo[b], self.hi[b]
+            self.X.append(xs)
+        self.idx = np.array([self.sub_index(e) for e in range(self.G)], dtype=np.int64).reshape(self.G, d)
+        self.mu = np.array([[0.5 * (self.X[b][i[b]] + self.X[b][i[b] + 1]) for b in range(d)] for i in self.idx])
+        self.sigma = np.array([[0.5 * (self.X[b][i[b] + 1] - self.X[b][i[b]]) for b in range(d)] for i in self.idx])
+        self.feats = philox.features(self.G, self.fields, self.M, d, float(desc["feat_range"]), desc["seed"])
+        self._build_rows()
+
+    # -- indexing ---------------------------------------------------------
+    def sub_index(self, e):
+        out = []
+        for b in reversed(range(self.d)):
+            out.append(e % self.N[b])
+            e //= self.N[b]
+        return tuple(reversed(out))
+
+    def sub_id(self, idx):
+        e = 0
+        for b in range(self.d):
+            e = e * self.N[b] + idx[b]
+        return e
+
+    def grid1d(self, b, j, q):
+        a, c = self.X[b][j], self.X[b][j + 1]
+        pts = [a + ((c - a) * p) / (q - 1) for p in range(q)]
+        pts[0], pts[-1] = a, c
+        return pts
+
+    # -- rows -------------------------------------------------------------
+    def _face_points(self, e, a, qs):
+        other = [b for b in range(self.d) if b != a]
+        idx = self.idx[e]
+        axes = [self.grid1d(b, idx[b], qs[b]) for b in other]
+        mesh = np.meshgrid(*axes, indexing="ij") if axes else []
+        cnt = int(np.prod([len(x) for x in axes])) if axes else 1
+        P = np.zeros((cnt, self.d))
+        for t, b in enumerate(other):
+            P[:, b] = mesh[t].reshape(-1)
+        return P
+
+    def _build_rows(self):
+        d = self.d
+        desc = self.desc
+        kind, e0, e1, axis, sord, field, side, pts = [], [], [], [], [], [], [], []
+
+        def add(P, k, a0, a1, ax, s, f, sd):
+            r = P.shape[0]
+            kind.append(np.full(r, k)); e0.append(np.full(r, a0)); e1.append(np.full(r, a1))
+            axis.append(np.full(r, ax)); sord.append(np.full(r, s)); field.append(np.full(r, f))
+            side.append(np.full(r, sd)); pts.append(P)
+
+        qi = desc["q_int"]
+        for e in range(self.G):
+            axes = [self.grid1d(b, self.idx[e][b], qi[b]) for b in range(d)]
+            mesh = np.meshgrid(*axes, indexing="ij")
+            P = np.stack([m.reshape(-1) for m in mesh], axis=1)
+            for f in range(self.fields):
+                add(P, 0, e, -1, -1, 0, f, -1)
+        self.m_int = sum(p.shape[0] for p in pts)
+        for a in range(d):
+            for e in range(self.G):
+                idx = list(self.idx[e])
+                if idx[a] >= self.N[a] - 1:
+                    continue
+                nb = list(idx); nb[a] += 1
+                e2 = self.sub_id(nb)
+                P = self._face_points(e, a, desc["q_iface"])
+                P[:, a] = self.X[a][idx[a] + 1]
+                for f in range(self.fields):
+                    for s in range(self.cont):
+                        add(P, 1, e, e2, a, s, f, -1)
+        self.m_iface = sum(p.shape[0] for p in pts) - self.m_int
+        for a in range(d):
+            for sd in (0, 1):
+                for e in range(self.G):
+                    if self.idx[e][a] != (0 if sd == 0 else self.N[a] - 1):
+                        continue
+                    P = self._face_points(e, a, desc["q_bdy"])
+                    P[:, a] = self.lo[a] if sd == 0 else self.hi[a]
+                    for f in range(self.fields):
+                        add(P, 2, e, -1, a, 0, f, sd)
+        cat = np.concatenate
+        self.rkind = cat(kind); self.re0 = cat(e0); self.re1 = cat(e1)
+        self.raxis = cat(axis); self.rsord = cat(sord); self.rfield = cat(field)
+        self.rside = cat(side); self.rx = cat(pts, axis=0)
+        self.m = self.rx.shape[0]
+        self.m_bdy = self.m - self.m_int - self.m_iface
+
+    # -- manufactured data --------------------------------------------------
+    def exact(self, X):
+        """Manufactured solution at points X [npts, d] -> [npts, fields]
+        (kind 3 has none and returns NaN)."""
+        k = self.kind
+        S = np.ones(X.shape[0])
+        for b in range(self.d):
+            S = S * np.sin(math.pi * X[:, b])
+        if k in (0, 2):
+            return S[:, None]
+        if k == 1:
+            x, y, z = X[:, 0], X[:, 1], X[:, 2]
+            u = np.sin(x * (1 - x)) * np.sin(y * (1 - y)) * np.exp(z)
+            return np.stack([u, S], axis=1)
+        return np.full((X.shape[0], 1), np.nan)
+
+    def source(self, X, f):
+        """Right-hand side f of the PDE for field f at interior points."""
+        k, p, d = self.kind, self.params, self.d
+        pi = math.pi
+        if k == 0:
+            u = self.exact(X)[:, 0]
+            return d * pi * pi * u + p[0] * u ** 3
+        if k == 2:
+            u = self.exact(X)[:, 0]
+            a = 1.0 + 0.5 * np.sin(2 * pi * X[:, 0])
+            ax = pi * np.cos(2 * pi * X[:, 0])
+            ux = pi * np.cos(pi * X[:, 0])
+            for b in range(1, d):
+                ux = ux * np.sin(pi * X[:, b])
+            return a * d * pi * pi * u - ax * ux + p[0] * u ** 3
+        if k == 3:
+            kap, A, q = p[0], p[1], p[2]
+            S = np.ones(X.shape[0])
+            for b in range(d):
+                S = S * np.sin(q * pi * X[:, b])
+            return A * S
+        if k == 1:
+            eu, ev, F, kk = p[0], p[1], p[2], p[3]
+            x, y, z = X[:, 0], X[:, 1], X[:, 2]
+            # u = sin(x(1-x)) sin(y(1-y)) e^z ; v = sin(pi x) sin(pi y) sin(pi z)
+            ax, ay = x * (1 - x), y * (1 - y)
+            sx, cx, sy, cy = np.sin(ax), np.cos(ax), np.sin(ay), np.cos(ay)
+            ez = np.exp(z)
+            u = sx * sy * ez
+            uxx = (-sx * (1 - 2 * x) ** 2 - 2 * cx) * sy * ez
+            uyy = sx * (-sy * (1 - 2 * y) ** 2 - 2 * cy) * ez
+            lap_u = uxx + uyy + u
+            v = np.sin(pi * x) * np.sin(pi * y) * np.sin(pi * z)
+            lap_v = -3 * pi * pi * v
+            if f == 0:
+                return -eu * lap_u + u * v * v - F * (1 - u)
+            return -ev * lap_v - u * v * v + (F + kk) * v
+        raise ValueError(k)
+
+    def boundary_data(self, X, f):
+        if self.kind == 3:
+            return np.zeros(X.shape[0])
+        return self.exact(X)[:, f]
