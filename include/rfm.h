@@ -1,0 +1,202 @@
+/*
+ * rfm.h -- C ABI of the GB300 (sm_103a) library for the random-feature-method
+ * nonlinear solvers IPN and AMIPN (arXiv 2510.04170, "Robust and efficient
+ * solvers for nonlinear PDEs based on random feature method").
+ *
+ * Conventions for every entry point
+ *  - Pointers named *_dev are device pointers (FP64 unless stated), contiguous,
+ *    owned by the caller; the library never frees them.  Pointers named *_host
+ *    are host memory.  The library owns every internal workspace of an
+ *    rfm_problem and frees it in rfm_problem_destroy.
+ *  - All device work is enqueued on the stream given to rfm_problem_create
+ *    (NULL = legacy default stream).  Entry points that return host scalars
+ *    synchronise that stream before returning.
+ *  - Errors are returned as rfm_status; rfm_last_error() gives a thread-local
+ *    message.  No entry point falls back to the CPU.
+ *  - Layouts: a problem has m collocation rows and n = G * fields * M unknowns,
+ *    ordered subdomain-major, then field, then feature.  Rows are ordered:
+ *    interior (subdomain, field, grid point), interface (normal axis, left
+ *    subdomain, field, derivative order, face point), boundary (axis, side lo/hi,
+ *    subdomain, field, face point).
+ */
+#ifndef RFM_H
+#define RFM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RFM_OK = 0,
+  RFM_EINVAL = 1,      /* bad argument or size                                  */
+  RFM_ENOMEM = 2,      /* device allocation failed                              */
+  RFM_ECUDA = 3,       /* a CUDA call failed                                    */
+  RFM_ENOCONV = 4,     /* solver hit its iteration cap (iterate still written)  */
+  RFM_ERANK = 5,       /* a pivot of R was floored (warning; result written)    */
+  RFM_ENONFINITE = 6,  /* a residual norm became NaN/Inf                        */
+  RFM_ETIMEOUT = 7     /* a bounded device wait gave up (result invalid)        */
+} rfm_status;
+
+typedef struct rfm_problem rfm_problem;
+
+/* Problem description (Sec. 2.2, Sec. 5): domain box [lo, hi], nsub[d]
+ * subdomains per axis, M tanh features per subdomain and field with k, b ~
+ * U[-feat_range, feat_range] drawn by Philox4x32-10 from `seed`; collocation
+ * grids with q_int[b] points per axis on each subdomain (endpoints included),
+ * q_bdy[b] / q_iface[b] points per axis on boundary / interface faces;
+ * cont_order continuity orders C^0..C^{k-1} across interfaces.
+ * pde_kind: 0 -Lap u + p0 u^3 = f; 1 Gray-Scott (2 fields: eps_u, eps_v, F, k);
+ *           2 -div(a grad u) + p0 u^3 = f, a = 1 + 0.5 sin(2 pi x);
+ *           3 kind 2 with source p1 prod sin(p2 pi x_d) and zero Dirichlet data. */
+typedef struct {
+  int dim;
+  double lo[3], hi[3];
+  int nsub[3];
+  int M;
+  int fields;
+  int q_int[3];
+  int q_bdy[3];
+  int q_iface[3];
+  int cont_order;
+  double feat_range;
+  uint64_t seed;
+  int pde_kind;
+  double pde_params[8];
+} rfm_problem_desc;
+
+enum { RFM_SKETCH_COUNT = 0, RFM_SKETCH_GAUSS = 1 };
+
+/* Solver options (Sec. 6 defaults: gamma 3, eta 1e-6, eps 1e-10, tau_rel 1e-3,
+ * m_max 3; row scale c 100, Sec. 5).  sketch_rows 0 means ceil(gamma n);
+ * lsqr_max_iter 0 means 2n.  precision 0 is FP64 throughout. */
+typedef struct {
+  int sketch_kind;
+  double gamma;
+  int64_t sketch_rows;
+  double eta;
+  double eps;
+  int max_outer;
+  int m_max;
+  double tau_rel;
+  double row_scale_c;
+  int precision;
+  int64_t lsqr_max_iter;
+  double conlim;
+} rfm_solve_opts;
+
+/* Per-solve record mirroring the paper's reported columns (IT, NJ, LSQR steps,
+ * preconditioning time, final ||F||).  Times in milliseconds (CUDA events). */
+typedef struct {
+  int status;
+  int outer_iters;          /* IT */
+  int n_jac;                /* NJ */
+  int lsqr_iters_total;
+  int lsqr_iters_max;
+  int rank_flag;
+  double final_resid;       /* ||W F(u)|| at the returned iterate */
+  double t_assemble, t_sketch, t_qr, t_lsqr, t_linesearch, t_total;
+} rfm_solve_info;
+
+void rfm_default_opts(rfm_solve_opts* opts);
+const char* rfm_last_error(void);
+
+/* Builds the problem: uploads the subdomain/row tables, then draws the
+ * features (Philox, Sec. 2.2) and the collocation points and right-hand sides
+ * (Sec. 5) on the device.  `cuda_stream` is a cudaStream_t or NULL.
+ * Errors: RFM_EINVAL for dim not in {2,3}, non-positive counts, fields not 1
+ * or 2, cont_order not in {1,2}; RFM_ENOMEM/RFM_ECUDA on device failures. */
+rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, rfm_problem** out);
+rfm_status rfm_problem_destroy(rfm_problem* p);
+
+/* m rows, n unknowns, W = fields*M (width of a column block), G subdomains,
+ * m_int / m_iface interior and interface row counts. */
+rfm_status rfm_problem_sizes(const rfm_problem* p, int64_t* m, int64_t* n, int64_t* W,
+                             int64_t* G, int64_t* m_int, int64_t* m_iface);
+
+/* Copies the feature table [G*fields*M][4] (k_1..k_d, b, zero padding) and
+ * the row points [m][4] (x_1..x_d, padding) to device buffers (Sec. 2.2). */
+rfm_status rfm_get_features(const rfm_problem* p, double* feat_dev);
+rfm_status rfm_get_points(const rfm_problem* p, double* pts_dev);
+
+/* Assembles F(c) and J(c) (Alg. 3 steps 1-4) and applies the row rescaling
+ * lambda_i = c_scale / max_j |J_ij| (Sec. 5) to both; keeps the scaled J and
+ * lambda inside the problem.  F_dev [m] (nullable) receives the scaled F,
+ * lam_dev [m] (nullable) the row scales. */
+rfm_status rfm_assemble(rfm_problem* p, const double* c_dev, double c_scale, double* F_dev, double* lam_dev);
+
+/* Copies the stored scaled Jacobian: Jp_dev [m][W] holds each row's primary
+ * block (columns of subdomain e0), Js_dev [m_iface][W] the secondary block of
+ * interface rows (subdomain e1); blk_dev (int32 [m][2], nullable) gets
+ * (e0, e1) with e1 = -1 for non-interface rows. */
+rfm_status rfm_get_jacobian(const rfm_problem* p, double* Jp_dev, double* Js_dev, int32_t* blk_dev);
+
+/* Scaled residual W F(c) with the stored row scales (no Jacobian).  F_dev [m]
+ * nullable; norm_host (nullable) receives ||W F(c)||. */
+rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, double* norm_host);
+
+/* Sketch of the stored scaled J for Jacobian evaluation kJ (Sec. 4.1):
+ * count sketch (B[h(i),:] += sigma(i) J[i,:]) or Gaussian sketch with
+ * bfloat16-exact N(0,1) entries.  s rows; B kept inside the problem as an
+ * s x n column-major matrix.  B_dev (nullable, [n][s] column-major) receives a
+ * copy. */
+rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev);
+
+/* Householder QR of the stored sketch (Sec. 4.1, thin QR B = QR); keeps R
+ * (upper triangular, positive diagonal, pivots below 1e-14 max R_jj floored)
+ * as the preconditioner.  R_dev (nullable, [n][n] column-major) receives R. */
+rfm_status rfm_qr(rfm_problem* p, double* R_dev);
+
+/* Installs a caller-supplied preconditioner R (n x n column-major upper). */
+rfm_status rfm_set_r(rfm_problem* p, const double* R_dev);
+
+/* Standalone Householder R of an s x n column-major matrix (ld = s), the same
+ * kernels as rfm_qr.  A_dev is overwritten; R_dev [n][n] column-major. */
+rfm_status rfm_householder_r(double* A_dev, int64_t s, int64_t n, void* cuda_stream, double* R_dev,
+                             int* rank_flag_host);
+
+/* y = J x (trans 0, x [n], y [m]) or y = J^T x (trans 1, x [m], y [n]) with
+ * the stored scaled J. */
+rfm_status rfm_jmv(rfm_problem* p, int trans, const double* x_dev, double* y_dev);
+
+/* x = R^{-1} b (trans 0) or x = R^{-T} b (trans 1) with the stored R. */
+rfm_status rfm_trsv(rfm_problem* p, int trans, const double* b_dev, double* x_dev);
+
+/* LSQR (Paige-Saunders) on J R^{-1} y ~ b with atol = btol = eta; returns the
+ * Newton direction d = R^{-1} y in d_dev [n] (Alg. 1 steps 3-4). */
+rfm_status rfm_lsqr(rfm_problem* p, const double* b_dev, double eta, double conlim, int64_t max_iter,
+                    double* d_dev, int* iters_host, int* istop_host);
+
+/* Golden-section line search on phi(alpha) = ||W F(c + alpha d)|| over [0,1]
+ * with the stored row scales (Alg. 1 step 5). */
+rfm_status rfm_linesearch(rfm_problem* p, const double* c_dev, const double* d_dev, double f0,
+                          double* alpha_host, double* fbest_host);
+
+/* IPN (Alg. 1) and AMIPN (Alg. 2) from the initial guess in c_dev [n]
+ * (overwritten with the result).  info (nullable) is filled. */
+rfm_status rfm_ipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_dev, rfm_solve_info* info);
+rfm_status rfm_amipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_dev, rfm_solve_info* info);
+
+/* u_n at query points (Sec. 2.2, Eq. 2.7 with the indicator PoU): pts_dev
+ * [npts][dim] row-major, u_dev [npts][fields]. */
+rfm_status rfm_eval(const rfm_problem* p, const double* c_dev, const double* pts_dev, int64_t npts,
+                    double* u_dev);
+
+/* Benchmark instrumentation (not part of the method).  rfm_profile_enable(mask)
+ * clears the counters and records a CUDA event pair around every launch of
+ * the kernel families whose bit is set in mask (0 disables), on the stream the
+ * kernel is launched on; rfm_profile_read synchronises and returns the
+ * family's total milliseconds and launch count.  Family names:
+ * rfm_profile_name(0 .. rfm_profile_count()-1).  rfm_launch_count() is the
+ * number of kernels this library has launched in the process so far. */
+rfm_status rfm_profile_enable(int mask);
+int64_t rfm_launch_count(void);
+int rfm_profile_count(void);
+const char* rfm_profile_name(int family);
+rfm_status rfm_profile_read(int family, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,97 @@
+// Optional per-kernel-family timing with CUDA events recorded on the stream
+// each kernel is launched on.  Disabled by default (zero overhead beyond one
+// branch per launch); a benchmark enables it, runs, then reads the totals.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "rfm_internal.cuh"
+
+namespace {
+
+const char* kNames[RFM_PROF_FAMILIES] = {"assemble",  "residual", "sketch_count", "sketch_gauss_gen", "sketch_gemm",
+                                         "qr_panel",  "qr_vta",   "qr_update",    "trsv",             "jmv",
+                                         "jtmv",      "ls_pre",   "ls_eval",      "vector",           "eval"};
+
+struct Rec {
+  int fam;
+  cudaEvent_t a, b;
+};
+
+std::mutex g_mu;
+bool g_on = false;
+unsigned int g_mask = 0;
+std::atomic<long long> g_launches{0};
+std::vector<Rec> g_recs;
+double g_ms[RFM_PROF_FAMILIES];
+long long g_cnt[RFM_PROF_FAMILIES];
+
+void drain_locked() {
+  for (Rec& r : g_recs) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    g_ms[r.fam] += ms;
+    g_cnt[r.fam] += 1;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_recs.clear();
+}
+
+}  // namespace
+
+void rfm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void* rfm_prof_begin(int fam, cudaStream_t st) {
+  if (!g_on || !((g_mask >> fam) & 1u)) return nullptr;
+  Rec* r = new Rec;
+  r->fam = fam;
+  cudaEventCreate(&r->a);
+  cudaEventCreate(&r->b);
+  cudaEventRecord(r->a, st);
+  return r;
+}
+
+void rfm_prof_end(void* h, cudaStream_t st) {
+  if (!h) return;
+  Rec* r = static_cast<Rec*>(h);
+  cudaEventRecord(r->b, st);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_recs.push_back(*r);
+  delete r;
+  if (g_recs.size() > 4096) drain_locked();
+}
+
+extern "C" {
+
+rfm_status rfm_profile_enable(int mask) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain_locked();
+  for (int i = 0; i < RFM_PROF_FAMILIES; ++i) {
+    g_ms[i] = 0.0;
+    g_cnt[i] = 0;
+  }
+  g_mask = (unsigned int)mask;
+  g_on = mask != 0;
+  return RFM_OK;
+}
+
+int64_t rfm_launch_count(void) { return g_launches.load(); }
+
+int rfm_profile_count(void) { return RFM_PROF_FAMILIES; }
+
+const char* rfm_profile_name(int family) {
+  return (family >= 0 && family < RFM_PROF_FAMILIES) ? kNames[family] : "";
+}
+
+rfm_status rfm_profile_read(int family, double* ms, int64_t* launches) {
+  if (family < 0 || family >= RFM_PROF_FAMILIES) return RFM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain_locked();
+  if (ms) *ms = g_ms[family];
+  if (launches) *launches = g_cnt[family];
+  return RFM_OK;
+}
+
+}  // extern "C"

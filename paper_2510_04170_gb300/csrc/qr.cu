@@ -1,0 +1,469 @@
+// Householder QR of the sketch B = S_k J (Sec. 4.1, "thin QR B = Q R") giving
+// the right preconditioner R.  Blocked right-looking Householder with the
+// compact-WY trailing update (Schreiber & Van Loan):
+//
+//   for each panel of NB columns:
+//     k_panel   (cooperative, one CTA per SM slice of rows): the panel's rows
+//               stay in shared memory; per column one bounded grid barrier
+//               combines the column norm, a second combines v^T A for the rest
+//               of the panel.  Reflector H = I - tau v v^T, v_0 = 1,
+//               beta = -sign(alpha) ||x||.  At the end T (NB x NB, upper) with
+//               T_jj = tau_j, T_{:j,j} = -tau_j T_{:j,:j} V_{:,:j}^T v_j.
+//     k_vta     W_z = V^T A_trail over a K-slice z (split K, deterministic)
+//     k_wt      W2 = T^T sum_z W_z
+//     k_update  A_trail -= V W2
+//   k_normalise: flip rows of R to a positive diagonal, floor pivots below
+//               1e-14 max_j R_jj (rank guard; flag raised).
+//
+// All sums are reduced in a fixed order, so repeated runs give identical bits.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "rfm_internal.cuh"
+
+namespace {
+
+constexpr int NB = 32;
+
+struct PanelArgs {
+  double* A;
+  long long lda;
+  long long s;
+  long long j0;
+  int nbw;           // columns in this panel (<= NB)
+  int P;             // CTAs
+  int chunk;         // rows per CTA
+  double* part;      // [P][NB + 2]
+  double* gram;      // [P][NB*NB]
+  double* tau;       // [n]
+  double* T;         // [NB][NB] (row-major T[i][j])
+  unsigned int* bar;  // [2]: count, generation
+  unsigned int* err;
+};
+
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int* err) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g = ld_acquire(bar + 1);
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      st_release(bar + 1, g + 1);
+    } else {
+      wait_flag(bar + 1, g + 1, err);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+    if (lane == 0) sh[32] = r;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
+  extern __shared__ double sp[];  // [NB][chunk] column-major panel slice
+  __shared__ double sh[40];
+  __shared__ double sw[NB];
+  const int c = blockIdx.x;
+  const long long rbeg = a.j0 + (long long)c * a.chunk;
+  const long long rend = min(a.s, rbeg + a.chunk);
+  const int nr = rbeg < rend ? (int)(rend - rbeg) : 0;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int chunk = a.chunk;
+  for (int jj = 0; jj < a.nbw; ++jj) {
+    const double* col = a.A + (size_t)(a.j0 + jj) * a.lda + rbeg;
+    for (int r = tid; r < nr; r += blockDim.x) sp[jj * chunk + r] = col[r];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < a.nbw; ++jj) {
+    const long long j = a.j0 + jj;  // pivot row
+    double* v = sp + jj * chunk;
+    double loc = 0.0;
+    for (int r = tid; r < nr; r += blockDim.x)
+      if (rbeg + r > j) loc += v[r] * v[r];
+    loc = block_sum(loc, sh);
+    if (tid == 0) {
+      const bool own = j >= rbeg && j < rend;
+      a.part[c * (NB + 2) + 0] = loc;
+      a.part[c * (NB + 2) + 1] = own ? v[j - rbeg] : 0.0;
+    }
+    grid_barrier(a.bar, a.P, a.err);
+    double sigma = 0.0, alpha = 0.0;
+    for (int q = 0; q < a.P; ++q) {
+      sigma += __ldcg(a.part + q * (NB + 2));
+      alpha += __ldcg(a.part + q * (NB + 2) + 1);
+    }
+    double tau = 0.0, beta = alpha, scale = 0.0;
+    if (sigma != 0.0) {
+      const double nrm = sqrt(alpha * alpha + sigma);
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    // v_r = x_r / (alpha - beta) below the pivot, v_j = 1
+    if (tau != 0.0)
+      for (int r = tid; r < nr; r += blockDim.x)
+        if (rbeg + r > j) v[r] *= scale;
+    __syncthreads();
+    // partial w_k = sum_{r >= j} v_r A[r, k] for the remaining panel columns
+    const int rest = a.nbw - jj - 1;
+    for (int kk = w; kk < rest; kk += (blockDim.x >> 5)) {
+      const double* ck = sp + (jj + 1 + kk) * chunk;
+      double acc = 0.0;
+      for (int r = lane; r < nr; r += 32) {
+        const long long gr = rbeg + r;
+        if (gr >= j) acc += (gr == j ? 1.0 : v[r]) * ck[r];
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) a.part[c * (NB + 2) + 2 + kk] = acc;
+    }
+    grid_barrier(a.bar, a.P, a.err);
+    for (int kk = tid; kk < rest; kk += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < a.P; ++q) s += __ldcg(a.part + q * (NB + 2) + 2 + kk);
+      sw[kk] = s;
+    }
+    __syncthreads();
+    if (tau != 0.0) {
+      for (int kk = 0; kk < rest; ++kk) {
+        const double f = tau * sw[kk];
+        double* ck = sp + (jj + 1 + kk) * chunk;
+        for (int r = tid; r < nr; r += blockDim.x) {
+          const long long gr = rbeg + r;
+          if (gr >= j) ck[r] -= (gr == j ? 1.0 : v[r]) * f;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && j >= rbeg && j < rend) v[j - rbeg] = beta;
+    if (c == 0 && tid == 0) a.tau[j] = tau;
+    __syncthreads();
+  }
+  // partial Gram V^T V of this CTA's rows (v_j = 1 on the pivot, 0 above)
+  for (int pq = tid; pq < a.nbw * a.nbw; pq += blockDim.x) {
+    const int p = pq / a.nbw, q = pq % a.nbw;
+    double acc = 0.0;
+    if (p <= q) {
+      for (int r = 0; r < nr; ++r) {
+        const long long gr = rbeg + r;
+        const double vp = gr < a.j0 + p ? 0.0 : (gr == a.j0 + p ? 1.0 : sp[p * chunk + r]);
+        const double vq = gr < a.j0 + q ? 0.0 : (gr == a.j0 + q ? 1.0 : sp[q * chunk + r]);
+        acc += vp * vq;
+      }
+    }
+    a.gram[(size_t)c * NB * NB + pq] = acc;
+  }
+  // write the panel back (R entries on and above the diagonal, v below)
+  for (int jj = 0; jj < a.nbw; ++jj) {
+    double* col = a.A + (size_t)(a.j0 + jj) * a.lda + rbeg;
+    for (int r = tid; r < nr; r += blockDim.x) col[r] = sp[jj * chunk + r];
+  }
+  grid_barrier(a.bar, a.P, a.err);
+  if (c == 0) {
+    __shared__ double G[NB][NB + 1];
+    __shared__ double Ts[NB][NB + 1];
+    for (int pq = tid; pq < a.nbw * a.nbw; pq += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < a.P; ++q) s += __ldcg(a.gram + (size_t)q * NB * NB + pq);
+      G[pq / a.nbw][pq % a.nbw] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int jj = 0; jj < a.nbw; ++jj) {
+        const double tj = __ldcg(a.tau + a.j0 + jj);
+        for (int i = 0; i < jj; ++i) {
+          double s = 0.0;
+          for (int l = i; l < jj; ++l) s += Ts[i][l] * G[l][jj];
+          Ts[i][jj] = -tj * s;
+        }
+        Ts[jj][jj] = tj;
+        for (int i = jj + 1; i < a.nbw; ++i) Ts[i][jj] = 0.0;
+      }
+    }
+    __syncthreads();
+    for (int pq = tid; pq < NB * NB; pq += blockDim.x) {
+      const int p = pq / NB, q = pq % NB;
+      a.T[pq] = (p < a.nbw && q < a.nbw) ? Ts[p][q] : 0.0;
+    }
+  }
+}
+
+// Vector of panel column p at global row gr (unit pivot, zero above).
+__device__ __forceinline__ double vval(const double* A, long long lda, long long j0, int p, long long gr) {
+  const long long piv = j0 + p;
+  if (gr < piv) return 0.0;
+  if (gr == piv) return 1.0;
+  return A[(size_t)(j0 + p) * lda + gr];
+}
+
+// Wp[z][p][col] = sum_{r in K-slice z} v_p(r) A[r, j1 + col]
+__global__ void __launch_bounds__(256) k_vta(const double* __restrict__ A, long long lda, long long s, long long j0,
+                                             int nbw, long long j1, long long nt, long long kchunk,
+                                             double* __restrict__ Wp) {
+  __shared__ double Vs[32][NB + 1];
+  __shared__ double As[32][64 + 1];
+  const int tid = threadIdx.x;
+  const long long col0 = (long long)blockIdx.x * 64;
+  const int z = blockIdx.y;
+  const long long kb = j0 + (long long)z * kchunk;
+  const long long ke = min(s, kb + kchunk);
+  const int ay = tid >> 4, cx = tid & 15;
+  double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (long long r0 = kb; r0 < ke; r0 += 32) {
+    for (int idx = tid; idx < 32 * NB; idx += 256) {
+      const int rr = idx & 31, p = idx >> 5;
+      const long long gr = r0 + rr;
+      Vs[rr][p] = (gr < ke && p < nbw) ? vval(A, lda, j0, p, gr) : 0.0;
+    }
+    for (int idx = tid; idx < 32 * 64; idx += 256) {
+      const int rr = idx & 31, cc = idx >> 5;
+      const long long gr = r0 + rr, gc = col0 + cc;
+      As[rr][cc] = (gr < ke && gc < nt) ? A[(size_t)(j1 + gc) * lda + gr] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const double v0 = Vs[rr][ay], v1 = Vs[rr][ay + 16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double av = As[rr][cx + 16 * q];
+        acc[0][q] += v0 * av;
+        acc[1][q] += v1 * av;
+      }
+    }
+    __syncthreads();
+  }
+  for (int h = 0; h < 2; ++h)
+    for (int q = 0; q < 4; ++q) {
+      const long long gc = col0 + cx + 16 * q;
+      const int p = ay + 16 * h;
+      if (gc < nt) Wp[((size_t)z * NB + p) * nt + gc] = acc[h][q];
+    }
+}
+
+// W2[p][col] = sum_q T[q][p] sum_z Wp[z][q][col]
+__global__ void k_wt(const double* __restrict__ Wp, int nz, const double* __restrict__ T, int nbw, long long nt,
+                     double* __restrict__ W2) {
+  const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (col >= nt) return;
+  double wv[NB];
+  for (int q = 0; q < NB; ++q) {
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += Wp[((size_t)z * NB + q) * nt + col];
+    wv[q] = s;
+  }
+  for (int p = 0; p < NB; ++p) {
+    double s = 0.0;
+    for (int q = 0; q <= p && q < nbw; ++q) s += T[q * NB + p] * wv[q];
+    W2[(size_t)p * nt + col] = p < nbw ? s : 0.0;
+  }
+}
+
+// A[r, j1 + col] -= sum_p v_p(r) W2[p][col] for r in [j0, s)
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ A, long long lda, long long s, long long j0,
+                                                int nbw, long long j1, long long nt, const double* __restrict__ W2) {
+  __shared__ double Vs[NB][128];
+  __shared__ double Ws[NB][64];
+  const int tid = threadIdx.x;
+  const long long r0 = j0 + (long long)blockIdx.x * 128;
+  const long long c0 = (long long)blockIdx.y * 64;
+  for (int idx = tid; idx < NB * 128; idx += 256) {
+    const int rr = idx & 127, p = idx >> 7;
+    const long long gr = r0 + rr;
+    Vs[p][rr] = (gr < s && p < nbw) ? vval(A, lda, j0, p, gr) : 0.0;
+  }
+  for (int idx = tid; idx < NB * 64; idx += 256) {
+    const int cc = idx & 63, p = idx >> 6;
+    const long long gc = c0 + cc;
+    Ws[p][cc] = gc < nt ? W2[(size_t)p * nt + gc] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid & 31, ty = tid >> 5;
+  double acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[i][q] = 0.0;
+#pragma unroll 4
+  for (int p = 0; p < NB; ++p) {
+    double vv[4], ww[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) vv[i] = Vs[p][tx + 32 * i];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ww[q] = Ws[p][ty + 8 * q];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[i][q] += vv[i] * ww[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long gc = c0 + ty + 8 * q;
+    if (gc >= nt) continue;
+    double* colp = A + (size_t)(j1 + gc) * lda;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long gr = r0 + tx + 32 * i;
+      if (gr < s) colp[gr] -= acc[i][q];
+    }
+  }
+}
+
+__global__ void k_diag(const double* __restrict__ A, long long lda, long long n, double* __restrict__ dg) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dg[i] = A[(size_t)i * lda + i];
+}
+
+// Flip row i of R when R_ii < 0 (upper triangle only).
+__global__ void k_flip(double* __restrict__ A, long long lda, long long n, const double* __restrict__ dg) {
+  const long long col = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= col; i += (long long)gridDim.x * blockDim.x)
+    if (dg[i] < 0.0) A[(size_t)col * lda + i] = -A[(size_t)col * lda + i];
+}
+
+__global__ void k_floor(double* __restrict__ A, long long lda, long long n, unsigned int* flag) {
+  __shared__ double sh[40];
+  double mx = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, A[(size_t)i * lda + i]);
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    v = warp_max(v);
+    if (threadIdx.x == 0) sh[32] = v;
+  }
+  __syncthreads();
+  const double fl = 1e-14 * sh[32];
+  for (long long i = threadIdx.x; i < n; i += blockDim.x)
+    if (A[(size_t)i * lda + i] < fl) {
+      A[(size_t)i * lda + i] = fl;
+      atomicExch(flag, 1u);
+    }
+}
+
+struct QrScratch {
+  double* part;
+  double* gram;
+  double* tau;
+  double* T;
+  double* Wp;
+  double* W2;
+  double* dg;
+};
+
+int g_num_sms = 0;
+int g_panel_occ = 0;
+
+}  // namespace
+
+long long rfm_householder_scratch(long long s, long long n) {
+  const long long P = 1024;
+  const long long maxz = 64;
+  return P * (NB + 2) + P * NB * NB + n + NB * NB + maxz * NB * n + NB * n + n + 64;
+}
+
+rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda, cudaStream_t st,
+                                   double* scratch, long long scratch_len, unsigned int* sync, int* rank_flag_host) {
+  if (s < n || n <= 0) {
+    rfm_set_error("householder: need s >= n > 0");
+    return RFM_EINVAL;
+  }
+  if (scratch_len < rfm_householder_scratch(s, n)) {
+    rfm_set_error("householder: scratch too small");
+    return RFM_EINVAL;
+  }
+  if (g_num_sms == 0) {
+    int dev = 0;
+    RFM_CUDA(cudaGetDevice(&dev));
+    RFM_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    RFM_CUDA(cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  }
+  QrScratch q;
+  double* w = scratch;
+  q.part = w; w += 1024 * (NB + 2);
+  q.gram = w; w += 1024LL * NB * NB;
+  q.tau = w; w += n;
+  q.T = w; w += NB * NB;
+  q.Wp = w; w += 64LL * NB * n;
+  q.W2 = w; w += (long long)NB * n;
+  q.dg = w;
+  unsigned int* bar = sync + SYNC_BAR;
+  unsigned int* err = sync + SYNC_ERR;
+  RFM_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), st));
+  for (long long j0 = 0; j0 < n; j0 += NB) {
+    const int nbw = (int)std::min<long long>(NB, n - j0);
+    const long long rows = s - j0;
+    // rows per CTA: at least 64, at most what fits in 200 KB of shared memory
+    const long long maxchunk = (200LL * 1024) / (NB * (long long)sizeof(double));
+    long long P = std::min<long long>((rows + 63) / 64, (long long)g_num_sms);
+    if (P < 1) P = 1;
+    long long chunk = (rows + P - 1) / P;
+    if (chunk > maxchunk) {
+      rfm_set_error("householder: sketch too tall for the panel kernel");
+      return RFM_EINVAL;
+    }
+    PanelArgs a;
+    a.A = A; a.lda = lda; a.s = s; a.j0 = j0; a.nbw = nbw; a.P = (int)P; a.chunk = (int)chunk;
+    a.part = q.part; a.gram = q.gram; a.tau = q.tau; a.T = q.T; a.bar = bar; a.err = err;
+    void* args[] = {&a};
+    const size_t smem = (size_t)NB * chunk * sizeof(double);
+    {
+      ProfScope ps(PF_QR_PANEL, st);
+      RFM_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel, dim3((unsigned)P), dim3(256), args, smem, st));
+      rfm_count_launch();
+    }
+    const long long j1 = j0 + nbw;
+    const long long nt = n - j1;
+    if (nt <= 0) break;
+    const long long ctiles = (nt + 63) / 64;
+    long long nz = (2LL * g_num_sms + ctiles - 1) / ctiles;
+    nz = std::max<long long>(1, std::min<long long>(nz, std::min<long long>(64, (rows + 255) / 256)));
+    const long long kchunk = (rows + nz - 1) / nz;
+    nz = (rows + kchunk - 1) / kchunk;
+    {
+      ProfScope ps(PF_QR_VTA, st);
+      k_vta<<<dim3((unsigned)ctiles, (unsigned)nz), 256, 0, st>>>(A, lda, s, j0, nbw, j1, nt, kchunk, q.Wp);
+      RFM_CHECK_LAUNCH();
+      k_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(q.Wp, (int)nz, q.T, nbw, nt, q.W2);
+      RFM_CHECK_LAUNCH();
+    }
+    ProfScope psu(PF_QR_UPDATE, st);
+    k_update<<<dim3((unsigned)((rows + 127) / 128), (unsigned)ctiles), 256, 0, st>>>(A, lda, s, j0, nbw, j1, nt, q.W2);
+    RFM_CHECK_LAUNCH();
+  }
+  k_diag<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, n, q.dg);
+  RFM_CHECK_LAUNCH();
+  k_flip<<<dim3((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n), 256, 0, st>>>(A, lda, n, q.dg);
+  RFM_CHECK_LAUNCH();
+  RFM_CUDA(cudaMemsetAsync(sync + SYNC_BAR + 2, 0, sizeof(unsigned int), st));
+  k_floor<<<1, 1024, 0, st>>>(A, lda, n, sync + SYNC_BAR + 2);
+  RFM_CHECK_LAUNCH();
+  if (rank_flag_host) {
+    unsigned int hv[2] = {0, 0};
+    RFM_CUDA(cudaMemcpyAsync(hv, sync + SYNC_BAR + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    RFM_CUDA(cudaMemcpyAsync(hv + 1, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    RFM_CUDA(cudaStreamSynchronize(st));
+    *rank_flag_host = (int)hv[0];
+    if (hv[1]) {
+      rfm_set_error("householder: a grid barrier timed out");
+      return RFM_ETIMEOUT;
+    }
+  }
+  return RFM_OK;
+}

@@ -1,0 +1,186 @@
+// Internal declarations shared by the CUDA translation units of librfm.
+// Hot-path kernels for the random feature method with the IPN / AMIPN solvers
+// (arXiv 2510.04170): assembly (Alg. 3), sketch + QR preconditioner (Sec. 4.1),
+// LSQR on J R^{-1} and the golden-section line search (Alg. 1, Alg. 2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rfm.h"
+
+#define RFM_MAX_FIELDS 2
+#define RFM_MAX_WIDTH 2048
+
+// One run of rows that share a point grid (Sec. 5): an interior grid of a
+// subdomain, or a face grid on an interface or a boundary face.
+struct RowSeg {
+  int kind;     // 0 interior, 1 interface, 2 boundary
+  int e0, e1;   // subdomain (left / own) and right neighbour (interface only)
+  int axis;     // normal axis of a face (-1 interior)
+  int sord;     // derivative order across an interface (0: C^0, 1: C^1)
+  int field;
+  int side;     // boundary side 0 lo, 1 hi
+  int q[3];     // points per axis (face grids: along the axes != axis)
+  int pad;
+  long long row0;
+  long long count;
+};
+
+struct rfm_problem {
+  rfm_problem_desc desc;
+  cudaStream_t stream;
+  int d, G, M, fields, W, nmaxbp;
+  int N[3];
+  long long n, m, m_int, m_iface, m_bdy;
+  // device tables
+  double* X = nullptr;      // breakpoints [3][nmaxbp]
+  double* mu = nullptr;     // [G][4]
+  double* sig = nullptr;    // [G][4]
+  double* feat = nullptr;   // [G*fields*M][4]
+  RowSeg* segs = nullptr;
+  int nseg = 0;
+  double* pts = nullptr;    // [m][4]
+  int4* rmeta = nullptr;    // per row: {kind|field<<4|axis<<8|sord<<12|side<<16, e0, e1, 0}
+  double* rhs = nullptr;    // [m] source f (interior) or boundary data g
+  // Jacobian (scaled) and residual
+  double* Jp = nullptr;     // [m][W]
+  double* Js = nullptr;     // [m_iface][W]
+  double* lam = nullptr;    // [m]
+  double* F = nullptr;      // [m]
+  bool have_j = false;
+  int* colptr = nullptr;    // [G+1] transposed block structure
+  int* colrows = nullptr;   // row | (secondary << 31)
+  // sketch / QR
+  long long s = 0, s_cap = 0;
+  double* B = nullptr;      // s x n column-major (R in its upper triangle after QR)
+  uint16_t* Sg = nullptr;   // Gaussian sketch, bf16 bits, [m][s]
+  long long sg_cap = 0;
+  int* hbuck = nullptr;     // count sketch buckets [m]
+  double* hsign = nullptr;  // [m]
+  int* bptr = nullptr;      // [s+1]
+  int* brows = nullptr;     // [m]
+  long long bptr_cap = 0;
+  double* R = nullptr;      // points into B (ld = ldr) or into Rown
+  double* Rown = nullptr;
+  long long ldr = 0;
+  bool have_r = false;
+  int rank_flag = 0;
+  // scratch
+  double* work = nullptr;   // general vectors
+  long long work_cap = 0;
+  double* red = nullptr;    // reduction partials
+  unsigned int* sync = nullptr;  // counters / flags / error words
+  unsigned int epoch = 0;
+  double* hostbuf = nullptr;     // pinned host scalars
+};
+
+// ---- error handling --------------------------------------------------------
+void rfm_set_error(const std::string& msg);
+#define RFM_CUDA(call)                                                          \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      rfm_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+      return RFM_ECUDA;                                                         \
+    }                                                                           \
+  } while (0)
+void rfm_count_launch();
+#define RFM_CHECK_LAUNCH()                                                      \
+  do {                                                                          \
+    rfm_count_launch();                                                         \
+    cudaError_t e_ = cudaGetLastError();                                        \
+    if (e_ != cudaSuccess) {                                                    \
+      rfm_set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));   \
+      return RFM_ECUDA;                                                         \
+    }                                                                           \
+  } while (0)
+#define RFM_TRY(x)                 \
+  do {                             \
+    rfm_status s_ = (x);           \
+    if (s_ != RFM_OK) return s_;   \
+  } while (0)
+
+// ---- optional per-kernel-family timing (prof.cu) -----------------------------
+enum {
+  PF_ASSEMBLE = 0, PF_RESIDUAL, PF_SKETCH_COUNT, PF_SKETCH_GEN, PF_SKETCH_GEMM, PF_QR_PANEL, PF_QR_VTA,
+  PF_QR_UPDATE, PF_TRSV, PF_JMV, PF_JTMV, PF_LS_PRE, PF_LS_EVAL, PF_VECTOR, PF_EVAL, RFM_PROF_FAMILIES
+};
+void* rfm_prof_begin(int fam, cudaStream_t st);
+void rfm_prof_end(void* h, cudaStream_t st);
+struct ProfScope {
+  void* h;
+  cudaStream_t st;
+  ProfScope(int fam, cudaStream_t s) : h(rfm_prof_begin(fam, s)), st(s) {}
+  ~ProfScope() { rfm_prof_end(h, st); }
+};
+
+// ---- launchers implemented in the .cu files -----------------------------------
+rfm_status rfm_launch_setup(rfm_problem* p);                        // features, points, rhs
+rfm_status rfm_launch_assemble(rfm_problem* p, const double* c, double cscale, bool want_j,
+                               const double* lam_in, double* Fout);
+rfm_status rfm_launch_ls_precompute(rfm_problem* p, const double* c, const double* dvec, double* P0,
+                                    double* P1, double* U, double* V);
+rfm_status rfm_launch_ls_eval(rfm_problem* p, const double* P0, const double* P1, const double* U,
+                              const double* V, double alpha, double* out_dev);
+rfm_status rfm_launch_eval(const rfm_problem* p, const double* c, const double* pts, long long npts,
+                           double* u);
+rfm_status rfm_launch_jmv(rfm_problem* p, const double* x, double* y);
+rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y);
+rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x);
+rfm_status rfm_launch_count_sketch(rfm_problem* p, long long s, int kJ);
+rfm_status rfm_launch_gauss_sketch(rfm_problem* p, long long s, int kJ);
+rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda,
+                                   cudaStream_t st, double* scratch, long long scratch_len,
+                                   unsigned int* sync, int* rank_flag_host);
+long long rfm_householder_scratch(long long s, long long n);
+// deterministic norms / dots: result written to out_dev[0]
+rfm_status rfm_norm2(cudaStream_t st, const double* x, long long n, double* partial, double* out_dev);
+rfm_status rfm_dot(cudaStream_t st, const double* x, const double* y, long long n, double* partial,
+                   double* out_dev);
+
+// ---- device helpers ------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait until *flag == want.  Returns false (and records the failure in
+// *err) after ~2^22 polls, so a missing producer never hangs the GPU.
+__device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want,
+                                          unsigned int* err) {
+  unsigned int spins = 0;
+  while (ld_acquire(flag) != want) {
+    if (++spins > (1u << 22)) {
+      atomicExch(err, 1u);
+      return false;
+    }
+    if (spins > 64) __nanosleep(64);
+  }
+  return true;
+}
+#endif
+
+#define RFM_SYNC_WORDS 4096
+// layout of p->sync
+#define SYNC_ERR 0
+#define SYNC_TICKET 8
+#define SYNC_BAR 16
+#define SYNC_FLAGS 64

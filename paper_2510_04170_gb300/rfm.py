@@ -1,0 +1,271 @@
+"""Thin ctypes binding of librfm (include/rfm.h).  Names mirror the C entry
+points; every call only marshals arguments (torch tensors give device
+pointers and streams) and raises RfmError on a non-OK status.  There is no
+CPU path: loading fails loudly when the library is missing."""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librfm.so")
+
+RFM_OK, RFM_EINVAL, RFM_ENOMEM, RFM_ECUDA, RFM_ENOCONV, RFM_ERANK, RFM_ENONFINITE, RFM_ETIMEOUT = range(8)
+SKETCH = {"count": 0, "gauss": 1}
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ERANK", "ENONFINITE", "ETIMEOUT"]
+
+EXPORTS = ["rfm_default_opts", "rfm_last_error", "rfm_problem_create", "rfm_problem_destroy", "rfm_problem_sizes",
+           "rfm_get_features", "rfm_get_points", "rfm_assemble", "rfm_get_jacobian", "rfm_residual", "rfm_sketch",
+           "rfm_qr", "rfm_set_r", "rfm_householder_r", "rfm_jmv", "rfm_trsv", "rfm_lsqr", "rfm_linesearch",
+           "rfm_ipn_solve", "rfm_amipn_solve", "rfm_eval"]
+
+
+class RfmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("nsub", ctypes.c_int * 3), ("M", ctypes.c_int), ("fields", ctypes.c_int),
+                ("q_int", ctypes.c_int * 3), ("q_bdy", ctypes.c_int * 3), ("q_iface", ctypes.c_int * 3),
+                ("cont_order", ctypes.c_int), ("feat_range", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("pde_kind", ctypes.c_int), ("pde_params", ctypes.c_double * 8)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("sketch_kind", ctypes.c_int), ("gamma", ctypes.c_double), ("sketch_rows", ctypes.c_int64),
+                ("eta", ctypes.c_double), ("eps", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("m_max", ctypes.c_int), ("tau_rel", ctypes.c_double), ("row_scale_c", ctypes.c_double),
+                ("precision", ctypes.c_int), ("lsqr_max_iter", ctypes.c_int64), ("conlim", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("n_jac", ctypes.c_int),
+                ("lsqr_iters_total", ctypes.c_int), ("lsqr_iters_max", ctypes.c_int), ("rank_flag", ctypes.c_int),
+                ("final_resid", ctypes.c_double), ("t_assemble", ctypes.c_double), ("t_sketch", ctypes.c_double),
+                ("t_qr", ctypes.c_double), ("t_lsqr", ctypes.c_double), ("t_linesearch", ctypes.c_double),
+                ("t_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Loads librfm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librfm.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, D, I64, I, VP = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "rfm_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
+        "rfm_last_error": (ctypes.c_char_p, []),
+        "rfm_problem_create": (I, [ctypes.POINTER(ProblemDesc), VP, ctypes.POINTER(P)]),
+        "rfm_problem_destroy": (I, [P]),
+        "rfm_problem_sizes": (I, [P] + [ctypes.POINTER(I64)] * 6),
+        "rfm_get_features": (I, [P, VP]),
+        "rfm_get_points": (I, [P, VP]),
+        "rfm_assemble": (I, [P, VP, D, VP, VP]),
+        "rfm_get_jacobian": (I, [P, VP, VP, VP]),
+        "rfm_residual": (I, [P, VP, VP, ctypes.POINTER(D)]),
+        "rfm_sketch": (I, [P, I, I64, I, VP]),
+        "rfm_qr": (I, [P, VP]),
+        "rfm_set_r": (I, [P, VP]),
+        "rfm_householder_r": (I, [VP, I64, I64, VP, VP, ctypes.POINTER(I)]),
+        "rfm_jmv": (I, [P, I, VP, VP]),
+        "rfm_trsv": (I, [P, I, VP, VP]),
+        "rfm_lsqr": (I, [P, VP, D, D, I64, VP, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "rfm_linesearch": (I, [P, VP, VP, D, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "rfm_ipn_solve": (I, [P, ctypes.POINTER(SolveOpts), VP, ctypes.POINTER(SolveInfo)]),
+        "rfm_amipn_solve": (I, [P, ctypes.POINTER(SolveOpts), VP, ctypes.POINTER(SolveInfo)]),
+        "rfm_eval": (I, [P, VP, VP, I64, VP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, ok=(RFM_OK,)):
+    if st not in ok:
+        raise RfmError(st, load().rfm_last_error().decode())
+    return st
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype not in (torch.float64, torch.int32) or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float64/int32 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_desc(d):
+    D = ProblemDesc()
+    D.dim = d["dim"]
+    for b in range(3):
+        D.lo[b] = d["lo"][b] if b < d["dim"] else 0.0
+        D.hi[b] = d["hi"][b] if b < d["dim"] else 1.0
+        D.nsub[b] = d["nsub"][b] if b < d["dim"] else 1
+        D.q_int[b] = d["q_int"][b] if b < d["dim"] else 1
+        D.q_bdy[b] = d["q_bdy"][b] if b < d["dim"] else 1
+        D.q_iface[b] = d["q_iface"][b] if b < d["dim"] else 1
+    D.M, D.fields, D.cont_order = d["M"], d["fields"], d["cont_order"]
+    D.feat_range, D.seed, D.pde_kind = d["feat_range"], d["seed"], d["pde_kind"]
+    for i in range(8):
+        D.pde_params[i] = d["pde_params"][i]
+    return D
+
+
+def make_opts(o):
+    O = SolveOpts()
+    load().rfm_default_opts(ctypes.byref(O))
+    O.sketch_kind = SKETCH[o.get("sketch_kind", "count")]
+    O.gamma = o.get("gamma", 3.0)
+    O.sketch_rows = o.get("sketch_rows", 0)
+    O.eta, O.eps = o.get("eta", 1e-6), o.get("eps", 1e-10)
+    O.max_outer, O.m_max = o.get("max_outer", 50), o.get("m_max", 3)
+    O.tau_rel, O.row_scale_c = o.get("tau_rel", 1e-3), o.get("row_scale_c", 100.0)
+    O.precision = o.get("precision", 0)
+    O.lsqr_max_iter, O.conlim = o.get("lsqr_max_iter", 0), o.get("conlim", 1e8)
+    return O
+
+
+class Problem:
+    """Owns an rfm_problem.  `desc` is a problem dict (rfm_workloads)."""
+
+    def __init__(self, desc, stream=None):
+        lib = load()
+        self.desc = desc
+        self.stream = stream
+        self._h = ctypes.c_void_p()
+        _check(lib.rfm_problem_create(ctypes.byref(make_desc(desc)), _stream(stream), ctypes.byref(self._h)))
+        v = [ctypes.c_int64() for _ in range(6)]
+        _check(lib.rfm_problem_sizes(self._h, *[ctypes.byref(x) for x in v]))
+        self.m, self.n, self.W, self.G, self.m_int, self.m_iface = (x.value for x in v)
+
+    def close(self):
+        if self._h:
+            load().rfm_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, *shape, dtype=torch.float64):
+        return torch.empty(*shape, dtype=dtype, device="cuda")
+
+    # -- A1: features and points
+    def rfm_get_features(self):
+        out = self._dev(self.G * self.desc["fields"] * self.desc["M"], 4)
+        _check(load().rfm_get_features(self._h, _ptr(out)))
+        return out
+
+    def rfm_get_points(self):
+        out = self._dev(self.m, 4)
+        _check(load().rfm_get_points(self._h, _ptr(out)))
+        return out
+
+    # -- A2/A3: assembly with row scaling
+    def rfm_assemble(self, c, c_scale=100.0):
+        F, lam = self._dev(self.m), self._dev(self.m)
+        _check(load().rfm_assemble(self._h, _ptr(c), c_scale, _ptr(F), _ptr(lam)))
+        return F, lam
+
+    def rfm_get_jacobian(self):
+        Jp = self._dev(self.m, self.W)
+        Js = self._dev(max(1, self.m_iface), self.W)
+        blk = self._dev(self.m, 2, dtype=torch.int32)
+        _check(load().rfm_get_jacobian(self._h, _ptr(Jp), _ptr(Js), _ptr(blk)))
+        return Jp, Js[: self.m_iface], blk
+
+    def rfm_residual(self, c):
+        F = self._dev(self.m)
+        nv = ctypes.c_double()
+        _check(load().rfm_residual(self._h, _ptr(c), _ptr(F), ctypes.byref(nv)))
+        return F, nv.value
+
+    # -- A4/A5: sketch and QR
+    def rfm_sketch(self, kind, s, kJ, copy_out=True):
+        B = self._dev(self.n, s) if copy_out else None
+        _check(load().rfm_sketch(self._h, SKETCH[kind], s, kJ, _ptr(B)))
+        return B
+
+    def rfm_qr(self, copy_out=True):
+        R = self._dev(self.n, self.n) if copy_out else None
+        st = _check(load().rfm_qr(self._h, _ptr(R)), ok=(RFM_OK, RFM_ERANK))
+        return R, st == RFM_ERANK
+
+    def rfm_set_r(self, R_colmajor):
+        _check(load().rfm_set_r(self._h, _ptr(R_colmajor)))
+
+    # -- A6/A7: matvecs, triangular solves, LSQR
+    def rfm_jmv(self, x, trans=0):
+        y = self._dev(self.n if trans else self.m)
+        _check(load().rfm_jmv(self._h, trans, _ptr(x), _ptr(y)))
+        return y
+
+    def rfm_trsv(self, b, trans=0):
+        x = self._dev(self.n)
+        _check(load().rfm_trsv(self._h, trans, _ptr(b), _ptr(x)))
+        return x
+
+    def rfm_lsqr(self, b, eta=1e-6, conlim=1e8, max_iter=0):
+        d = self._dev(self.n)
+        it, istop = ctypes.c_int(), ctypes.c_int()
+        _check(load().rfm_lsqr(self._h, _ptr(b), eta, conlim, max_iter, _ptr(d), ctypes.byref(it), ctypes.byref(istop)))
+        return d, it.value, istop.value
+
+    # -- A8: line search
+    def rfm_linesearch(self, c, d, f0):
+        a, fb = ctypes.c_double(), ctypes.c_double()
+        _check(load().rfm_linesearch(self._h, _ptr(c), _ptr(d), f0, ctypes.byref(a), ctypes.byref(fb)))
+        return a.value, fb.value
+
+    # -- A9/A10: solvers
+    def _solve(self, fn, opts, c0):
+        c = torch.zeros(self.n, dtype=torch.float64, device="cuda") if c0 is None else c0.clone()
+        info = SolveInfo()
+        st = fn(self._h, ctypes.byref(make_opts(opts)), _ptr(c), ctypes.byref(info))
+        _check(st, ok=(RFM_OK, RFM_ENOCONV))
+        return c, info.as_dict()
+
+    def rfm_ipn_solve(self, opts, c0=None):
+        return self._solve(load().rfm_ipn_solve, opts, c0)
+
+    def rfm_amipn_solve(self, opts, c0=None):
+        return self._solve(load().rfm_amipn_solve, opts, c0)
+
+    # -- A11: evaluation
+    def rfm_eval(self, c, pts):
+        pts = pts.contiguous()
+        u = self._dev(pts.shape[0], self.desc["fields"])
+        _check(load().rfm_eval(self._h, _ptr(c), _ptr(pts), pts.shape[0], _ptr(u)))
+        return u
+
+
+def rfm_householder_r(A_colmajor, s, n, stream=None):
+    """R of an s x n column-major matrix given as a CUDA tensor of shape
+    (n, s) (A is overwritten)."""
+    R = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    flag = ctypes.c_int()
+    _check(load().rfm_householder_r(_ptr(A_colmajor), s, n, _stream(stream), _ptr(R), ctypes.byref(flag)))
+    return R, bool(flag.value)
