@@ -156,6 +156,26 @@ rfm_status rfm_set_r(rfm_problem* p, const double* R_dev);
 rfm_status rfm_householder_r(double* A_dev, int64_t s, int64_t n, void* cuda_stream, double* R_dev,
                              int* rank_flag_host);
 
+/* Householder R of an s x n column-major matrix exactly like
+ * rfm_householder_r, but without allocating device memory: for callers that
+ * cannot call cudaMalloc while they run, such as services that reserve all
+ * device memory up front in their own pool (where an allocation fails, or
+ * implicitly synchronises the device and stalls other streams) and loops with
+ * fixed latency budgets.  The paper has no counterpart; this is a deployment
+ * variant of the QR step.
+ *  - n <= 512 (RFM_EINVAL with a message otherwise); s >= n.
+ *  - Scratch is a fixed 17.2 MB file-scope device array (plus 16 KB of barrier
+ *    words) present on every GPU that loads the library until process exit.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - All calls share the array, which keeps the last call's contents: calls
+ *    that overlap on the GPU (two streams or two host threads) race and must be
+ *    serialised by the caller.
+ *  - A_dev is overwritten; R_dev [n][n] column-major; the stream is
+ *    synchronised before return. */
+rfm_status rfm_householder_r_noalloc(double* A_dev, int64_t s, int64_t n, void* cuda_stream, double* R_dev,
+                                     int* rank_flag_host);
+
 /* y = J x (trans 0, x [n], y [m]) or y = J^T x (trans 1, x [m], y [n]) with
  * the stored scaled J. */
 rfm_status rfm_jmv(rfm_problem* p, int trans, const double* x_dev, double* y_dev);

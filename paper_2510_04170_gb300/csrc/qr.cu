@@ -19,6 +19,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "rfm_internal.cuh"
 
@@ -465,5 +467,104 @@ rfm_status rfm_householder_inplace(double* A, long long s, long long n, long lon
       return RFM_ETIMEOUT;
     }
   }
+  return RFM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free Householder R.
+//
+// Same computation as rfm_householder_r, for callers that must not allocate
+// device memory while they run: services that reserve all device memory up
+// front through their own pool (where a cudaMalloc fails or implicitly
+// synchronises the device and stalls other streams), or loops with fixed
+// latency budgets.  The QR scratch lives in file-scope device arrays of fixed
+// size (17.2 MB of scratch + 16 KB of barrier words per GPU that loads the
+// library, held until the process exits), sized for n <= 512 columns.
+// Every call shares these arrays and they keep the last call's contents;
+// calls that overlap on the GPU (two streams, or two host threads) race on
+// them and must be serialised by the caller.
+#define RFM_NOALLOC_MAX_N 512
+#define RFM_NOALLOC_MAX_DEVICES 64
+
+namespace {
+constexpr long long kNoallocScratch = 1024LL * (NB + 2) + 1024LL * NB * NB + RFM_NOALLOC_MAX_N + NB * NB +
+                                      64LL * NB * RFM_NOALLOC_MAX_N + (long long)NB * RFM_NOALLOC_MAX_N +
+                                      RFM_NOALLOC_MAX_N + 64;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratch];
+static __device__ __align__(256) unsigned int g_noalloc_sync[RFM_SYNC_WORDS];
+
+namespace {
+
+struct NoallocDev {
+  double* scratch = nullptr;
+  unsigned int* sync = nullptr;
+};
+NoallocDev g_noalloc_dev[RFM_NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+__global__ void k_noalloc_copy_r(const double* __restrict__ A, long long lda, long long n, double* __restrict__ R) {
+  const long long col = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    R[(size_t)col * n + i] = i <= col ? A[(size_t)col * lda + i] : 0.0;
+}
+
+// Device addresses of the fixed arrays for the current device, resolved once
+// per device (host code must not pass the arrays' host-side names to kernels).
+rfm_status noalloc_setup(NoallocDev* out) {
+  int dev = 0;
+  RFM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= RFM_NOALLOC_MAX_DEVICES) {
+    rfm_set_error("rfm_householder_r_noalloc: device ordinal out of range");
+    return RFM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoallocDev& d = g_noalloc_dev[dev];
+  if (!d.scratch) {
+    void* ps = nullptr;
+    void* py = nullptr;
+    cudaError_t e1 = cudaGetSymbolAddress(&ps, g_noalloc_scratch);
+    if (e1 != cudaSuccess) {
+      rfm_set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e1));
+      return RFM_ECUDA;
+    }
+    cudaError_t e2 = cudaGetSymbolAddress(&py, g_noalloc_sync);
+    if (e2 != cudaSuccess) {
+      rfm_set_error(std::string("cudaGetSymbolAddress(sync): ") + cudaGetErrorString(e2));
+      return RFM_ECUDA;
+    }
+    d.scratch = static_cast<double*>(ps);
+    d.sync = static_cast<unsigned int*>(py);
+  }
+  *out = d;
+  return RFM_OK;
+}
+
+}  // namespace
+
+extern "C" rfm_status rfm_householder_r_noalloc(double* A_dev, int64_t s, int64_t n, void* cuda_stream,
+                                                double* R_dev, int* rank_flag_host) {
+  if (!A_dev || !R_dev || n <= 0 || s < n) {
+    rfm_set_error("rfm_householder_r_noalloc: need A, R and s >= n > 0");
+    return RFM_EINVAL;
+  }
+  if (n > RFM_NOALLOC_MAX_N) {
+    rfm_set_error("rfm_householder_r_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
+                  std::to_string(RFM_NOALLOC_MAX_N) + " columns; use rfm_householder_r");
+    return RFM_EINVAL;
+  }
+  NoallocDev d;
+  RFM_TRY(noalloc_setup(&d));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // barrier counters, flags and the error word must start at zero
+  RFM_CUDA(cudaMemsetAsync(d.sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st));
+  int flag = 0;
+  RFM_TRY(rfm_householder_inplace(A_dev, s, n, s, st, d.scratch, kNoallocScratch, d.sync, &flag));
+  dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
+  k_noalloc_copy_r<<<grid, 256, 0, st>>>(A_dev, s, n, R_dev);
+  RFM_CHECK_LAUNCH();
+  RFM_CUDA(cudaStreamSynchronize(st));
+  if (rank_flag_host) *rank_flag_host = flag;
   return RFM_OK;
 }
