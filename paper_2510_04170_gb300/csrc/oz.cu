@@ -1,0 +1,528 @@
+// FP64-accurate matrix products on the bf16 tensor cores (tcgen05), for the
+// dense contractions of the preconditioner: the sketch B = S_k J and the QR
+// trailing update (Sec. 4.1).
+//
+// Splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication", 2012):
+// every row i of A (over K) is scaled by 2^-e_i with max_k |A_ik| < 2^e_i and
+// written as digits  A_ik = 2^e_i sum_p a_p(i,k) 2^(-beta p)  with integers
+// |a_1| <= 2^beta, |a_p| <= 2^(beta-1) (nearest rounding, beta = 7), each exact
+// in bfloat16; B likewise per column.  Then
+//     (A B)_ij = 2^(e_i + f_j) sum_l 2^(-beta l) L_l(i,j),
+//     L_l = sum over digit pairs with p + q = l of a_p b_q,
+// and every L_l of the leading levels accumulated over a K-chunk of 512 is an
+// integer below 2^24, so its FP32 tensor-core accumulation is exact.  Levels
+// are combined per chunk (the four leading levels in FP64, the rest first in
+// FP32, whose rounding is then ~2^-52 of the leading term) and summed
+// over chunks in FP64; pairs with p + q > Lmax are dropped (their weight is
+// below 2^(-beta (Lmax+1)) relative to max|A_i.| max|B_.j|).
+//
+// Kernel layout: one CTA per 128 x 64 output tile, 6 warps.
+//   warp 0  producer: cp.async.bulk of pre-tiled digit tiles (16 KB A, 8 KB B)
+//           into shared memory, completion on mbarriers (expect_tx)
+//   warp 1  owns the 512-column TMEM allocation; lane 0 issues tcgen05.mma
+//           (kind::f16, bf16 x bf16 -> f32, M=128, N=64, K=16) for every digit
+//           pair into the TMEM accumulator of its level (64 columns each) and
+//           commits to mbarriers
+//   warps 2-5 epilogue: tcgen05.ld the levels of each chunk, combine, keep the
+//           FP64 running sums in registers, scale and write C
+// Digit tiles are K-major with 128-byte rows in the 128B-swizzle pattern so a
+// tile is one contiguous bulk copy and the UMMA shared-memory descriptor reads
+// it directly.  Every wait is bounded; on timeout an error word is set, the
+// CTA drains its copies (bounded), frees TMEM and exits.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "rfm_internal.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int ATILE = BM * BK * 2;  // 16384 bytes
+constexpr int BTILE = BN * BK * 2;  // 8192 bytes
+constexpr int MAXD = 8;             // digits per operand
+constexpr int ASTAGES = 4;
+constexpr int KCHUNK = 8;           // k-tiles per exact chunk (8 * 64 = 512)
+constexpr int BETA = 7;
+constexpr int kF64Levels = 4;       // levels combined in FP64 (the rest in FP32 first)
+constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
+
+__host__ __device__ __forceinline__ int swz128(int r, int k) {
+  const int chunk = k >> 3;
+  return (r >> 3) * 1024 + (r & 7) * 128 + (((chunk ^ (r & 7)) & 7) << 4) + ((k & 7) << 1);
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for completion of the phase with the given parity: gives up
+// after kWaitNs of wall time and records `code` in *err.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* err, unsigned code) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (unsigned i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 0 && gtimer() - t0 > kWaitNs) break;
+  }
+  atomicCAS(err, 0u, code);
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ uint64_t umma_desc(const void* smem_tile) {
+  const uint64_t addr = smem_u32(smem_tile);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;          // start address
+  d |= (uint64_t)1 << 16;                // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset: 8-row groups 1024 B apart
+  d |= (uint64_t)1 << 46;                // descriptor version
+  d |= (uint64_t)2 << 61;                // 128-byte swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: bf16 A and B (K-major), f32 accumulate, M=128, N=64.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- GEMM kernel
+struct OzArgs {
+  const uint16_t* A;  // digit tiles [pA][mtiles][ktiles][ATILE/2]
+  const uint16_t* B;  // digit tiles [pB][ntiles][ktiles][BTILE/2]
+  int pA, pB, Lmax;   // digits; keep pairs with p + q <= Lmax (p, q from 1)
+  int mtiles, ntiles, ktiles;
+  const int* ea;      // per row of A: exponent e_i
+  const int* eb;      // per column of B: exponent f_j
+  double* C;          // column-major, C[i + j * ldc]
+  long long ldc, M, N;
+  int mode;           // 0: C = AB, 1: C -= AB
+  unsigned* err;
+};
+
+struct __align__(8) OzBars {
+  uint64_t a_full[ASTAGES], a_empty[ASTAGES], b_full[2], b_empty[2], acc_full, acc_empty, fin;
+  uint32_t tmem_base;
+};
+
+__global__ void __launch_bounds__(192, 1) k_oz_gemm(OzArgs g) {
+  extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* abuf = smem;                          // ASTAGES * ATILE
+  unsigned char* bbuf = abuf + ASTAGES * ATILE;        // 2 * pB * BTILE
+  OzBars* bars = reinterpret_cast<OzBars*>(bbuf + 2 * MAXD * BTILE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  const int nlev = min(g.Lmax - 1, g.pA + g.pB - 1);
+  const int nchunks = (g.ktiles + KCHUNK - 1) / KCHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ASTAGES; ++s) {
+      mbar_init(&bars->a_full[s], 1);
+      mbar_init(&bars->a_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars->b_full[b], 1);
+      mbar_init(&bars->b_empty[b], 1);
+    }
+    mbar_init(&bars->acc_full, 1);
+    mbar_init(&bars->acc_empty, 4);
+    mbar_init(&bars->fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&bars->tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer
+      unsigned aidx = 0;
+      int kissued = 0;
+      bool ok = true;
+      for (int kt = 0; kt < g.ktiles && ok; ++kt) {
+        const int b = kt & 1;
+        const unsigned use_b = (unsigned)kt >> 1;
+        if (use_b > 0) ok = mbar_wait(&bars->b_empty[b], (use_b - 1) & 1, g.err, 2);
+        if (!ok) break;
+        mbar_expect_tx(&bars->b_full[b], (unsigned)(g.pB * BTILE));
+        kissued = kt + 1;
+        for (int q = 0; q < g.pB; ++q) {
+          const uint16_t* src = g.B + (((size_t)q * g.ntiles + nt) * g.ktiles + kt) * (BTILE / 2);
+          bulk_g2s(bbuf + (size_t)(b * MAXD + q) * BTILE, src, BTILE, &bars->b_full[b]);
+        }
+        for (int p = 0; p < g.pA && ok; ++p) {
+          const int s = aidx % ASTAGES;
+          const unsigned use = aidx / ASTAGES;
+          if (use > 0) ok = mbar_wait(&bars->a_empty[s], (use - 1) & 1, g.err, 3);
+          if (!ok) break;
+          mbar_expect_tx(&bars->a_full[s], (unsigned)ATILE);
+          const uint16_t* src = g.A + (((size_t)p * g.mtiles + mt) * g.ktiles + kt) * (ATILE / 2);
+          bulk_g2s(abuf + (size_t)s * ATILE, src, ATILE, &bars->a_full[s]);
+          ++aidx;
+        }
+      }
+      // drain: make sure no copy is still writing shared memory before exit
+      if (aidx > 0) {
+        for (unsigned t = (aidx > ASTAGES ? aidx - ASTAGES : 0); t < aidx; ++t)
+          mbar_wait(&bars->a_full[t % ASTAGES], (t / ASTAGES) & 1, g.err, 4);
+      }
+      for (int kt = (kissued > 2 ? kissued - 2 : 0); kt < kissued; ++kt)
+        mbar_wait(&bars->b_full[kt & 1], ((unsigned)kt >> 1) & 1, g.err, 5);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      unsigned aidx = 0;
+      unsigned initmask = 0;
+      bool ok = true;
+      int chunk = 0;
+      for (int kt = 0; kt < g.ktiles && ok; ++kt) {
+        if (kt > 0 && kt % KCHUNK == 0) {
+          umma_commit(&bars->acc_full);
+          ok = mbar_wait(&bars->acc_empty, (unsigned)chunk & 1, g.err, 6);
+          tc_fence_after();
+          ++chunk;
+          initmask = 0;
+          if (!ok) break;
+        }
+        const int b = kt & 1;
+        ok = mbar_wait(&bars->b_full[b], ((unsigned)kt >> 1) & 1, g.err, 7);
+        if (!ok) break;
+        for (int p = 0; p < g.pA && ok; ++p) {
+          const int s = aidx % ASTAGES;
+          ok = mbar_wait(&bars->a_full[s], (aidx / ASTAGES) & 1, g.err, 8);
+          if (!ok) break;
+          tc_fence_after();
+          const uint64_t ad = umma_desc(abuf + (size_t)s * ATILE);
+          for (int q = 0; q < g.pB; ++q) {
+            if (p + q + 2 > g.Lmax) break;
+            const int l = p + q;
+            const uint64_t bd = umma_desc(bbuf + (size_t)(b * MAXD + q) * BTILE);
+            const uint32_t first = (initmask >> l) & 1u ? 1u : 0u;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_bf16(tmem + (uint32_t)(l * BN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                        (first || kk > 0) ? 1u : 0u);
+            initmask |= 1u << l;
+          }
+          umma_commit(&bars->a_empty[s]);
+          ++aidx;
+        }
+        umma_commit(&bars->b_empty[b]);
+      }
+      umma_commit(&bars->acc_full);
+      // every MMA this thread issued has completed once `fin` fires
+      umma_commit(&bars->fin);
+      mbar_wait(&bars->fin, 0, g.err, 10);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5): TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
+    double acc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.0;
+    const float s32 = 1.0f / (float)(1 << BETA);
+    const double s64 = 1.0 / (double)(1 << BETA);
+    for (int c = 0; c < nchunks; ++c) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, (unsigned)c & 1, g.err, 9));
+      tc_fence_after();
+      if (ok) {
+#pragma unroll
+        for (int grp = 0; grp < BN / 16; ++grp) {
+          float t[16], v[16];
+          double x[16];
+          tmem_ld16(tmem + tlane + (uint32_t)((nlev - 1) * BN + grp * 16), t);
+          if (nlev - 1 >= kF64Levels) {
+            for (int l = nlev - 2; l >= kF64Levels; --l) {
+              tmem_ld16(tmem + tlane + (uint32_t)(l * BN + grp * 16), v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) t[i] = fmaf(t[i], s32, v[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = (double)t[i];
+            for (int l = kF64Levels - 1; l >= 0; --l) {
+              tmem_ld16(tmem + tlane + (uint32_t)(l * BN + grp * 16), v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) x[i] = fma(x[i], s64, (double)v[i]);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = (double)t[i];
+            for (int l = nlev - 2; l >= 0; --l) {
+              tmem_ld16(tmem + tlane + (uint32_t)(l * BN + grp * 16), v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) x[i] = fma(x[i], s64, (double)v[i]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[grp * 16 + i] += x[i];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->acc_empty);
+    }
+    const long long gi = (long long)mt * BM + row;
+    if (gi < g.M) {
+      const int ei = g.ea[gi];
+#pragma unroll
+      for (int j = 0; j < BN; ++j) {
+        const long long gj = (long long)nt * BN + j;
+        if (gj < g.N) {
+          const double val = ldexp(acc[j], ei + g.eb[gj] - 2 * BETA);
+          double* cp = g.C + gi + gj * g.ldc;
+          if (g.mode == 0) *cp = val;
+          else *cp -= val;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- slicing
+// Accessors give X(i, k) for row i (the M or N index) and reduction index k.
+struct AccStrided {  // X(i, k) = base[i * si + k * sk]
+  const double* base;
+  long long si, sk;
+  __device__ double operator()(long long i, long long k) const { return base[i * si + k * sk]; }
+};
+struct AccHouseVt {  // row i = Householder vector i of the panel at j0, k = row offset from j0
+  const double* A;
+  long long lda, j0;
+  __device__ double operator()(long long i, long long k) const {
+    if (k < i) return 0.0;
+    if (k == i) return 1.0;
+    return A[(size_t)(j0 + i) * lda + j0 + k];
+  }
+};
+struct AccHouseV {  // row i = matrix row j0 + i, k = panel column
+  const double* A;
+  long long lda, j0;
+  __device__ double operator()(long long i, long long k) const {
+    if (i < k) return 0.0;
+    if (i == k) return 1.0;
+    return A[(size_t)(j0 + k) * lda + j0 + i];
+  }
+};
+
+// e[i] = exponent with max_k |X(i,k)| < 2^e[i] (0 for a zero row).  One warp per row.
+template <class Acc>
+__global__ void k_rowexp(Acc X, long long R, long long K, int* __restrict__ e) {
+  const int lane = threadIdx.x & 31;
+  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < R;
+       i += (long long)gridDim.x * (blockDim.x >> 5)) {
+    double mx = 0.0;
+    for (long long k = lane; k < K; k += 32) mx = fmax(mx, fabs(X(i, k)));
+    mx = warp_max(mx);
+    if (lane == 0) {
+      int ex = 0;
+      if (mx > 0.0) frexp(mx, &ex);
+      e[i] = ex;
+    }
+  }
+}
+
+// Digit tiles: out[d][rtile][ktile][tile] with tile = TR rows x 64 k in the 128B swizzle.
+template <class Acc, int TR>
+__global__ void k_digits(Acc X, long long R, long long K, const int* __restrict__ e, int ndig, long long rtiles,
+                         long long ktiles, uint16_t* __restrict__ out) {
+  const long long total = rtiles * TR * ktiles * 64;
+  const size_t plane = (size_t)rtiles * ktiles * TR * 64;  // elements per digit plane
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    // t enumerates (rtile, ktile, r, k64) with k64 fastest
+    const int k64 = (int)(t & 63);
+    long long rest = t >> 6;
+    const int r = (int)(rest % TR);
+    rest /= TR;
+    const long long kt = rest % ktiles;
+    const long long rt = rest / ktiles;
+    const long long i = rt * TR + r, k = kt * 64 + k64;
+    double y = 0.0;
+    if (i < R && k < K) y = ldexp(X(i, k), -e[i]);
+    const size_t base = ((size_t)rt * ktiles + kt) * (TR * 64) + (size_t)(swz128(r, k64) >> 1);
+    for (int d = 0; d < ndig; ++d) {
+      const double s = y * (double)(1 << BETA);
+      const double dg = rint(s);
+      y = s - dg;
+      const float f = (float)dg;  // |dg| <= 128: exact in bf16
+      out[(size_t)d * plane + base] = (uint16_t)(__float_as_uint(f) >> 16);
+    }
+  }
+}
+
+int g_oz_attr = 0;
+
+size_t oz_smem_bytes() { return (size_t)ASTAGES * ATILE + 2 * MAXD * BTILE + sizeof(OzBars) + 1024; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows) {
+  const long long rt = (rows + tile_rows - 1) / tile_rows, kt = (K + 63) / 64;
+  return (long long)ndig * rt * kt * tile_rows * 64 * 2;
+}
+
+template <class Acc>
+static rfm_status slice(Acc X, long long R, long long K, int ndig, int tile_rows, int* e, uint16_t* out,
+                        cudaStream_t st) {
+  const int g1 = (int)std::min<long long>((R + 7) / 8, 152LL * 32);
+  k_rowexp<<<std::max(1, g1), 256, 0, st>>>(X, R, K, e);
+  RFM_CHECK_LAUNCH();
+  const long long rt = (R + tile_rows - 1) / tile_rows, kt = (K + 63) / 64;
+  const long long total = rt * tile_rows * kt * 64;
+  const int g2 = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+  if (tile_rows == BM)
+    k_digits<Acc, BM><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
+  else
+    k_digits<Acc, BN><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
+  RFM_CHECK_LAUNCH();
+  return RFM_OK;
+}
+
+rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, long long R, long long K, int ndig,
+                                int tile_rows, int* e, uint16_t* out, cudaStream_t st) {
+  return slice(AccStrided{base, si, sk}, R, K, ndig, tile_rows, e, out, st);
+}
+rfm_status rfm_oz_slice_house_vt(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
+                                 int* e, uint16_t* out, cudaStream_t st) {
+  return slice(AccHouseVt{A, lda, j0}, nb, K, ndig, BM, e, out, st);
+}
+rfm_status rfm_oz_slice_house_v(const double* A, long long lda, long long j0, long long rows, long long nb, int ndig,
+                                int* e, uint16_t* out, cudaStream_t st) {
+  return slice(AccHouseV{A, lda, j0}, rows, nb, ndig, BM, e, out, st);
+}
+
+rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
+                       long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
+                       unsigned* err, cudaStream_t st) {
+  if (pA < 1 || pB < 1 || pA > MAXD || pB > MAXD || Lmax < 2 || Lmax - 1 > 8) {
+    rfm_set_error("oz_gemm: bad digit counts");
+    return RFM_EINVAL;
+  }
+  if (!g_oz_attr) {
+    RFM_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes()));
+    g_oz_attr = 1;
+  }
+  OzArgs a;
+  a.A = Ad; a.B = Bd; a.pA = pA; a.pB = pB; a.Lmax = Lmax;
+  a.mtiles = (int)((M + BM - 1) / BM);
+  a.ntiles = (int)((N + BN - 1) / BN);
+  a.ktiles = (int)((K + BK - 1) / BK);
+  a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
+  if (a.ktiles == 0) return RFM_OK;
+  k_oz_gemm<<<dim3(a.mtiles, a.ntiles), 192, oz_smem_bytes(), st>>>(a);
+  RFM_CHECK_LAUNCH();
+  return RFM_OK;
+}
+
+// C (M x N, col-major ldc) = A (M x K, col-major lda) * B (K x N, col-major ldb)
+// emulated to FP64 accuracy with `digits` digits per operand.
+extern "C" rfm_status rfm_emulated_dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                                         int64_t ldc, int64_t M, int64_t N, int64_t K, int digits,
+                                         void* cuda_stream) {
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || digits < 1 || digits > MAXD || lda < M || ldb < K || ldc < M) {
+    rfm_set_error("rfm_emulated_dgemm: bad argument");
+    return RFM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const long long abytes = rfm_oz_digit_bytes(M, K, digits, BM);
+  const long long bbytes = rfm_oz_digit_bytes(N, K, digits, BN);
+  char* buf = nullptr;
+  const size_t total = (size_t)abytes + bbytes + (size_t)(M + N + 64) * sizeof(int) + 64;
+  if (cudaMalloc(&buf, total) != cudaSuccess) {
+    rfm_set_error("rfm_emulated_dgemm: allocation failed");
+    return RFM_ENOMEM;
+  }
+  uint16_t* Ad = reinterpret_cast<uint16_t*>(buf);
+  uint16_t* Bd = reinterpret_cast<uint16_t*>(buf + abytes);
+  int* ea = reinterpret_cast<int*>(buf + abytes + bbytes);
+  int* eb = ea + M;
+  unsigned* err = reinterpret_cast<unsigned*>(eb + N);
+  rfm_status s = RFM_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess) s = RFM_ECUDA;
+  // A rows over k: A[i + k*lda];  B columns over k: B[k + j*ldb]
+  if (s == RFM_OK) s = rfm_oz_slice_strided(A, 1, lda, M, K, digits, BM, ea, Ad, st);
+  if (s == RFM_OK) s = rfm_oz_slice_strided(B, ldb, 1, N, K, digits, BN, eb, Bd, st);
+  if (s == RFM_OK) s = rfm_oz_gemm(Ad, digits, ea, Bd, digits, eb, M, N, K, digits + 1, C, ldc, 0, err, st);
+  unsigned herr = 0;
+  if (s == RFM_OK) {
+    if (cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rfm_set_error(std::string("rfm_emulated_dgemm: ") + cudaGetErrorString(cudaGetLastError()));
+      s = RFM_ECUDA;
+    } else if (herr) {
+      rfm_set_error("rfm_emulated_dgemm: a bounded wait timed out (code " + std::to_string(herr) + ")");
+      s = RFM_ETIMEOUT;
+    }
+  }
+  cudaFree(buf);
+  return s;
+}

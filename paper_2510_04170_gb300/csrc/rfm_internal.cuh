@@ -162,8 +162,10 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// Bounded wait until *flag == want.  Returns false (and records the failure in
-// *err) after ~2^22 polls, so a missing producer never hangs the GPU.
+// Bounded wait until *flag == want.  Polls without sleeping first (a sleep's
+// granularity is far coarser than the expected wait), then backs off; gives up
+// after ~2^22 polls (well under a second of sleeping) and records the failure
+// in *err, so a missing producer never hangs the GPU.
 __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want,
                                           unsigned int* err) {
   unsigned int spins = 0;
@@ -172,7 +174,7 @@ __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int
       atomicExch(err, 1u);
       return false;
     }
-    if (spins > 64) __nanosleep(64);
+    if (spins > (1u << 16)) __nanosleep(128);
   }
   return true;
 }
