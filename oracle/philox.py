@@ -14,8 +14,10 @@ Stream layout (counter words c0..c3, key = (seed low word, seed high word)):
 
 The features are k, b ~ U[-R, R] (Sec. 2.2, Eq. 2.6); the sketch S_k is drawn
 afresh for every Jacobian evaluation (Sec. 4.1).  Gaussian sketch entries are
-Box-Muller normals rounded to bfloat16 (round to nearest even) so that they are
-exact in a 16-bit tensor-core operand.
+Box-Muller normals rounded to the grid 2^-4 (nearest, ties to even): each is an
+integer of magnitude at most 137 times 2^-4, i.e. one exact 8-bit digit of a
+fixed-point tensor-core product (the paper uses a count sketch and fixes no
+Gaussian variant; a rounded normal is still a sub-Gaussian embedding).
 
 Parity pinned by the published known-answer vectors of Philox4x32-10
 (tests/golden/philox4x32_10_kat.txt).
@@ -111,7 +113,8 @@ def round_bf16(x):
 def gaussian_sketch(s, rows, kJ, seed):
     """Columns `rows` of the Gaussian sketch S_k (s x m): entry (r, i) is the
     (r mod 2)-th Box-Muller normal of the pair drawn with counter
-    (2, i, r div 2, kJ), rounded to bfloat16.  Returns [s, len(rows)]."""
+    (2, i, r div 2, kJ), rounded to the nearest multiple of 2^-4.
+    Returns [s, len(rows)]."""
     assert s % 2 == 0
     k0, k1 = seed_key(seed)
     rows = np.asarray(rows, dtype=np.uint64)
@@ -124,4 +127,4 @@ def gaussian_sketch(s, rows, kJ, seed):
     out = np.empty((s, rows.size))
     out[0::2] = rad * np.cos(th)
     out[1::2] = rad * np.sin(th)
-    return round_bf16(out)
+    return np.rint(16.0 * out) / 16.0

@@ -7,7 +7,8 @@
 // (deterministic).  One warp per bucket accumulates into the column-major B.
 //
 // Gaussian sketch: S_k[r, i] is the (r mod 2)-th Box-Muller normal of Philox
-// counter (2, i, r/2, kJ), rounded to bfloat16, stored as bf16 bits [m][s].
+// counter (2, i, r/2, kJ), rounded to the grid 2^-4 (an integer of magnitude
+// <= 137 times 2^-4, exact in bf16), stored as bf16 bits [m][s].
 // B[:, block b] = S[:, rows(b)] J[rows(b), block b] for every column block b
 // (the rows touching subdomain b), an FP64 GEMM with gathered operands:
 // K = |rows(b)|, N = W, M = s.  Its algorithmic cost is 2 s nnz(J) flops.
@@ -117,8 +118,8 @@ __global__ void k_gauss_gen(long long m, long long s, uint32_t kJ, uint32_t key0
     const double u2 = uniform53(c[2], c[3]);
     const double rad = sqrt(-2.0 * log(1.0 - u1));
     const double th = 6.283185307179586 * u2;
-    const uint16_t z0 = bf16_bits_rne(rad * cos(th));
-    const uint16_t z1 = bf16_bits_rne(rad * sin(th));
+    const uint16_t z0 = bf16_bits_rne(rint(16.0 * (rad * cos(th))) * 0.0625);
+    const uint16_t z1 = bf16_bits_rne(rint(16.0 * (rad * sin(th))) * 0.0625);
     const uint32_t packed = (uint32_t)z0 | ((uint32_t)z1 << 16);
     reinterpret_cast<uint32_t*>(S + (size_t)i * s)[q] = packed;
   }
