@@ -70,7 +70,11 @@ enum { RFM_SKETCH_COUNT = 0, RFM_SKETCH_GAUSS = 1 };
 
 /* Solver options (Sec. 6 defaults: gamma 3, eta 1e-6, eps 1e-10, tau_rel 1e-3,
  * m_max 3; row scale c 100, Sec. 5).  sketch_rows 0 means ceil(gamma n);
- * lsqr_max_iter 0 means 2n.  precision 0 is FP64 throughout. */
+ * lsqr_max_iter 0 means 2n.  precision: 0 FP64 throughout; 1 the Gaussian
+ * sketch product S J on the bf16 tensor cores emulated to FP64 accuracy
+ * (digit splitting, exact level accumulation); 2 as 1 plus the QR trailing
+ * update on the tensor cores the same way.  Residual, line search, LSQR and
+ * the QR panels stay in FP64 at every level. */
 typedef struct {
   int sketch_kind;
   double gamma;
@@ -143,6 +147,10 @@ rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, doub
  * copy. */
 rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev);
 
+/* Precision level (see rfm_solve_opts.precision) used by rfm_sketch and
+ * rfm_qr; the solvers set it from their options.  RFM_EINVAL outside 0..2. */
+rfm_status rfm_set_precision(rfm_problem* p, int precision);
+
 /* Householder QR of the stored sketch (Sec. 4.1, thin QR B = QR); keeps R
  * (upper triangular, positive diagonal, pivots below 1e-14 max R_jj floored)
  * as the preconditioner.  R_dev (nullable, [n][n] column-major) receives R. */
@@ -155,6 +163,23 @@ rfm_status rfm_set_r(rfm_problem* p, const double* R_dev);
  * kernels as rfm_qr.  A_dev is overwritten; R_dev [n][n] column-major. */
 rfm_status rfm_householder_r(double* A_dev, int64_t s, int64_t n, void* cuda_stream, double* R_dev,
                              int* rank_flag_host);
+
+/* Householder R of an s x n column-major matrix (ld = s) with the trailing
+ * update on the bf16 tensor cores emulated to FP64 accuracy (the precision-2
+ * path of rfm_qr): 128-column outer blocks, FP64 panels inside a block, then
+ * W = V^T A, W2 = T^T W, A -= V W2 as split products.  A_dev is overwritten;
+ * R_dev [n][n] column-major.  Errors as rfm_householder_r. */
+rfm_status rfm_householder_r_tc(double* A_dev, int64_t s, int64_t n, void* cuda_stream, double* R_dev,
+                                int* rank_flag_host);
+
+/* C (M x N, column-major, ldc) = A (M x K, lda) B (K x N, ldb), all FP64,
+ * computed on the bf16 tensor cores by splitting each row of A and column of
+ * B into `digits` 7-bit integer digits (exact in bf16) whose level sums are
+ * accumulated exactly over 512-deep K chunks and combined in FP64 (1 <=
+ * digits <= 8; 8 gives FP64-class error relative to |A||B|).  Allocates its
+ * digit buffers; synchronises the stream. */
+rfm_status rfm_emulated_dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                              int64_t M, int64_t N, int64_t K, int digits, void* cuda_stream);
 
 /* Householder R of an s x n column-major matrix exactly like
  * rfm_householder_r, but without allocating device memory: for callers that

@@ -277,7 +277,7 @@ rfm_status ensure_sketch(rfm_problem* p, long long s, int kind) {
     RFM_TRY(dalloc(&p->brows, (size_t)p->m + 2 * s + 2));
     p->bptr_cap = s + 1;
   }
-  if (kind == RFM_SKETCH_GAUSS && s > p->sg_cap) {
+  if (kind == RFM_SKETCH_GAUSS && p->precision == 0 && s > p->sg_cap) {
     dfree(p->Sg);
     p->Sg = nullptr;
     p->sg_cap = 0;
@@ -310,7 +310,8 @@ rfm_status do_sketch(rfm_problem* p, int kind, long long s, int kJ) {
   RFM_TRY(ensure_sketch(p, s, kind));
   p->s = s;
   if (kind == RFM_SKETCH_COUNT) return rfm_launch_count_sketch(p, s, kJ);
-  if (kind == RFM_SKETCH_GAUSS) return rfm_launch_gauss_sketch(p, s, kJ);
+  if (kind == RFM_SKETCH_GAUSS)
+    return p->precision >= 1 ? rfm_launch_gauss_sketch_tc(p, s, kJ) : rfm_launch_gauss_sketch(p, s, kJ);
   g_err = "unknown sketch kind";
   return RFM_EINVAL;
 }
@@ -318,7 +319,23 @@ rfm_status do_sketch(rfm_problem* p, int kind, long long s, int kJ) {
 rfm_status do_qr(rfm_problem* p) {
   RFM_TRY(ensure_qr_scratch(p->s, p->n));
   int flag = 0;
-  RFM_TRY(rfm_householder_inplace(p->B, p->s, p->n, p->s, p->stream, g_qr_scratch, g_qr_scratch_len, p->sync, &flag));
+  if (p->precision >= 2) {
+    const long long need = rfm_householder_emulated_bytes(p->s, p->n);
+    if (need > p->qr_emu_bytes) {
+      dfree(p->qr_emu);
+      p->qr_emu = nullptr;
+      p->qr_emu_bytes = 0;
+      char* buf = nullptr;
+      RFM_TRY(dalloc(&buf, (size_t)need));
+      p->qr_emu = buf;
+      p->qr_emu_bytes = need;
+    }
+    RFM_TRY(rfm_householder_emulated(p->B, p->s, p->n, p->s, p->stream, g_qr_scratch, g_qr_scratch_len, p->sync,
+                                     p->qr_emu, p->qr_emu_bytes, &flag));
+  } else {
+    RFM_TRY(
+        rfm_householder_inplace(p->B, p->s, p->n, p->s, p->stream, g_qr_scratch, g_qr_scratch_len, p->sync, &flag));
+  }
   p->R = p->B;
   p->ldr = p->s;
   p->have_r = true;
@@ -522,6 +539,7 @@ rfm_status scaled_residual_norm(rfm_problem* p, const double* c, double* Fout, d
 
 bool validate_opts(const rfm_solve_opts* o) {
   return o && (o->sketch_kind == RFM_SKETCH_COUNT || o->sketch_kind == RFM_SKETCH_GAUSS) && o->eta > 0 &&
+         o->precision >= 0 && o->precision <= 2 &&
          o->max_outer > 0 && o->m_max > 0 && o->row_scale_c > 0 && (o->sketch_rows > 0 || o->gamma >= 1.0);
 }
 
@@ -601,6 +619,7 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
       colrows.insert(colrows.end(), lists[b].begin(), lists[b].end());
     }
   }
+  p->colptr_h = colptr;
   rfm_status st = RFM_OK;
 #define TRYA(x)                       \
   do {                                \
@@ -674,7 +693,7 @@ rfm_status rfm_problem_destroy(rfm_problem* p) {
   else cudaDeviceSynchronize();
   void* bufs[] = {p->X, p->mu, p->sig, p->feat, p->segs, p->pts, p->rmeta, p->rhs, p->Jp, p->Js, p->lam, p->F,
                   p->colptr, p->colrows, p->B, p->Sg, p->hbuck, p->hsign, p->bptr, p->brows, p->Rown, p->work,
-                  p->red, p->sync};
+                  p->red, p->sync, p->sdig, p->jdig, p->oz_e, p->oz_toff, p->qr_emu};
   for (void* b : bufs) dfree(b);
   if (p->hostbuf) cudaFreeHost(p->hostbuf);
   delete p;
@@ -753,6 +772,15 @@ rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, doub
   return RFM_OK;
 }
 
+rfm_status rfm_set_precision(rfm_problem* p, int precision) {
+  if (!p || precision < 0 || precision > 2) {
+    g_err = "rfm_set_precision: precision must be 0, 1 or 2";
+    return RFM_EINVAL;
+  }
+  p->precision = precision;
+  return RFM_OK;
+}
+
 rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev) {
   if (!p) return RFM_EINVAL;
   RFM_TRY(do_sketch(p, kind, s, kJ));
@@ -812,6 +840,34 @@ rfm_status rfm_householder_r(double* A_dev, int64_t s, int64_t n, void* cuda_str
   return r;
 }
 
+rfm_status rfm_householder_r_tc(double* A_dev, int64_t s, int64_t n, void* cuda_stream, double* R_dev,
+                                int* rank_flag_host) {
+  if (!A_dev || !R_dev || s < n || n <= 0) {
+    g_err = "rfm_householder_r_tc: bad argument";
+    return RFM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  RFM_TRY(ensure_qr_scratch(s, n));
+  unsigned int* sync = nullptr;
+  char* emu = nullptr;
+  const long long eb = rfm_householder_emulated_bytes(s, n);
+  RFM_TRY(dalloc(&sync, RFM_SYNC_WORDS));
+  rfm_status r = dalloc(&emu, (size_t)eb);
+  int flag = 0;
+  if (r == RFM_OK && cudaMemsetAsync(sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st) != cudaSuccess) r = RFM_ECUDA;
+  if (r == RFM_OK) r = rfm_householder_emulated(A_dev, s, n, s, st, g_qr_scratch, g_qr_scratch_len, sync, emu, eb, &flag);
+  if (r == RFM_OK) {
+    dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
+    k_copy_r<<<grid, 256, 0, st>>>(A_dev, s, n, R_dev);
+    rfm_count_launch();
+    if (cudaStreamSynchronize(st) != cudaSuccess) r = RFM_ECUDA;
+  }
+  cudaFree(sync);
+  if (emu) cudaFree(emu);
+  if (rank_flag_host) *rank_flag_host = flag;
+  return r;
+}
+
 rfm_status rfm_jmv(rfm_problem* p, int trans, const double* x_dev, double* y_dev) {
   if (!p || !p->have_j || !x_dev || !y_dev) return RFM_EINVAL;
   RFM_TRY(trans ? rfm_launch_jtmv(p, x_dev, y_dev) : rfm_launch_jmv(p, x_dev, y_dev));
@@ -852,6 +908,7 @@ rfm_status rfm_ipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_d
   }
   rfm_solve_info info;
   memset(&info, 0, sizeof(info));
+  p->precision = opts->precision;
   const long long n = p->n, m = p->m;
   double* b = wv(p, WV_B);
   double* d = wv(p, WV_D);
@@ -900,6 +957,7 @@ rfm_status rfm_amipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c
   }
   rfm_solve_info info;
   memset(&info, 0, sizeof(info));
+  p->precision = opts->precision;
   const long long n = p->n, m = p->m;
   double* d = wv(p, WV_D);
   double* z = wv(p, WV_Z);

@@ -48,10 +48,7 @@ constexpr int BETA = 7;
 constexpr int kF64Levels = 4;       // levels combined in FP64 (the rest in FP32 first)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
 
-__host__ __device__ __forceinline__ int swz128(int r, int k) {
-  const int chunk = k >> 3;
-  return (r >> 3) * 1024 + (r & 7) * 128 + (((chunk ^ (r & 7)) & 7) << 4) + ((k & 7) << 1);
-}
+__device__ __forceinline__ int swz128(int r, int k) { return rfm_swz128(r, k); }
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -372,6 +369,20 @@ struct AccHouseV {  // row i = matrix row j0 + i, k = panel column
   }
 };
 
+struct AccJBlock {  // row j = column j of a Jacobian column block, k = k-th row touching the block
+  const double* Jp;
+  const double* Js;
+  const int* rows;
+  long long m_int;
+  int W;
+  __device__ double operator()(long long j, long long k) const {
+    const unsigned ent = (unsigned)rows[k];
+    const long long r = ent & 0x7fffffffu;
+    const double* row = (ent >> 31) ? Js + (size_t)(r - m_int) * W : Jp + (size_t)r * W;
+    return row[j];
+  }
+};
+
 // e[i] = exponent with max_k |X(i,k)| < 2^e[i] (0 for a zero row).  One warp per row.
 template <class Acc>
 __global__ void k_rowexp(Acc X, long long R, long long K, int* __restrict__ e) {
@@ -433,6 +444,7 @@ long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_row
 template <class Acc>
 static rfm_status slice(Acc X, long long R, long long K, int ndig, int tile_rows, int* e, uint16_t* out,
                         cudaStream_t st) {
+  ProfScope ps(PF_OZ_SLICE, st);
   const int g1 = (int)std::min<long long>((R + 7) / 8, 152LL * 32);
   k_rowexp<<<std::max(1, g1), 256, 0, st>>>(X, R, K, e);
   RFM_CHECK_LAUNCH();
@@ -460,6 +472,11 @@ rfm_status rfm_oz_slice_house_v(const double* A, long long lda, long long j0, lo
   return slice(AccHouseV{A, lda, j0}, rows, nb, ndig, BM, e, out, st);
 }
 
+rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* rows, long long K, long long m_int,
+                               int W, int ndig, int* e, uint16_t* out, cudaStream_t st) {
+  return slice(AccJBlock{Jp, Js, rows, m_int, W}, W, K, ndig, BN, e, out, st);
+}
+
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
                        unsigned* err, cudaStream_t st) {
@@ -478,6 +495,7 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
   a.ktiles = (int)((K + BK - 1) / BK);
   a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
   if (a.ktiles == 0) return RFM_OK;
+  ProfScope ps(PF_OZ_GEMM, st);
   k_oz_gemm<<<dim3(a.mtiles, a.ntiles), 192, oz_smem_bytes(), st>>>(a);
   RFM_CHECK_LAUNCH();
   return RFM_OK;

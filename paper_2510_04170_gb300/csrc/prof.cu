@@ -11,7 +11,8 @@ namespace {
 
 const char* kNames[RFM_PROF_FAMILIES] = {"assemble",  "residual", "sketch_count", "sketch_gauss_gen", "sketch_gemm",
                                          "qr_panel",  "qr_vta",   "qr_update",    "trsv",             "jmv",
-                                         "jtmv",      "ls_pre",   "ls_eval",      "vector",           "eval"};
+                                         "jtmv",      "ls_pre",   "ls_eval",      "vector",           "eval",
+                                         "oz_gemm",   "oz_slice"};
 
 struct Rec {
   int fam;

@@ -380,22 +380,9 @@ long long rfm_householder_scratch(long long s, long long n) {
   return P * (NB + 2) + P * NB * NB + n + NB * NB + maxz * NB * n + NB * n + n + 64;
 }
 
-rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda, cudaStream_t st,
-                                   double* scratch, long long scratch_len, unsigned int* sync, int* rank_flag_host) {
-  if (s < n || n <= 0) {
-    rfm_set_error("householder: need s >= n > 0");
-    return RFM_EINVAL;
-  }
-  if (scratch_len < rfm_householder_scratch(s, n)) {
-    rfm_set_error("householder: scratch too small");
-    return RFM_EINVAL;
-  }
-  if (g_num_sms == 0) {
-    int dev = 0;
-    RFM_CUDA(cudaGetDevice(&dev));
-    RFM_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    RFM_CUDA(cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  }
+namespace {
+
+QrScratch carve(double* scratch, long long n) {
   QrScratch q;
   double* w = scratch;
   q.part = w; w += 1024 * (NB + 2);
@@ -405,11 +392,28 @@ rfm_status rfm_householder_inplace(double* A, long long s, long long n, long lon
   q.Wp = w; w += 64LL * NB * n;
   q.W2 = w; w += (long long)NB * n;
   q.dg = w;
+  return q;
+}
+
+rfm_status qr_init_device() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    RFM_CUDA(cudaGetDevice(&dev));
+    RFM_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    RFM_CUDA(cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  }
+  return RFM_OK;
+}
+
+// Householder factorisation of columns [c0, c1) (rows c0..s) in NB-wide
+// panels; the FP64 compact-WY update of each panel is applied to the columns
+// up to cend (cend >= c1).
+rfm_status factor_range(double* A, long long s, long long lda, long long c0, long long c1, long long cend,
+                        cudaStream_t st, const QrScratch& q, unsigned int* sync) {
   unsigned int* bar = sync + SYNC_BAR;
   unsigned int* err = sync + SYNC_ERR;
-  RFM_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), st));
-  for (long long j0 = 0; j0 < n; j0 += NB) {
-    const int nbw = (int)std::min<long long>(NB, n - j0);
+  for (long long j0 = c0; j0 < c1; j0 += NB) {
+    const int nbw = (int)std::min<long long>(NB, c1 - j0);
     const long long rows = s - j0;
     // rows per CTA: at least 64, at most what fits in 200 KB of shared memory
     const long long maxchunk = (200LL * 1024) / (NB * (long long)sizeof(double));
@@ -431,8 +435,8 @@ rfm_status rfm_householder_inplace(double* A, long long s, long long n, long lon
       rfm_count_launch();
     }
     const long long j1 = j0 + nbw;
-    const long long nt = n - j1;
-    if (nt <= 0) break;
+    const long long nt = cend - j1;
+    if (nt <= 0) continue;
     const long long ctiles = (nt + 63) / 64;
     long long nz = (2LL * g_num_sms + ctiles - 1) / ctiles;
     nz = std::max<long long>(1, std::min<long long>(nz, std::min<long long>(64, (rows + 255) / 256)));
@@ -449,6 +453,12 @@ rfm_status rfm_householder_inplace(double* A, long long s, long long n, long lon
     k_update<<<dim3((unsigned)((rows + 127) / 128), (unsigned)ctiles), 256, 0, st>>>(A, lda, s, j0, nbw, j1, nt, q.W2);
     RFM_CHECK_LAUNCH();
   }
+  return RFM_OK;
+}
+
+// Positive diagonal and pivot floor; reads back the rank flag and the error word.
+rfm_status finish_r(double* A, long long n, long long lda, cudaStream_t st, const QrScratch& q, unsigned int* sync,
+                    int* rank_flag_host) {
   k_diag<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, n, q.dg);
   RFM_CHECK_LAUNCH();
   k_flip<<<dim3((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n), 256, 0, st>>>(A, lda, n, q.dg);
@@ -459,15 +469,34 @@ rfm_status rfm_householder_inplace(double* A, long long s, long long n, long lon
   if (rank_flag_host) {
     unsigned int hv[2] = {0, 0};
     RFM_CUDA(cudaMemcpyAsync(hv, sync + SYNC_BAR + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-    RFM_CUDA(cudaMemcpyAsync(hv + 1, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    RFM_CUDA(cudaMemcpyAsync(hv + 1, sync + SYNC_ERR, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     RFM_CUDA(cudaStreamSynchronize(st));
     *rank_flag_host = (int)hv[0];
     if (hv[1]) {
-      rfm_set_error("householder: a grid barrier timed out");
+      rfm_set_error("householder: a bounded device wait timed out (code " + std::to_string(hv[1]) + ")");
       return RFM_ETIMEOUT;
     }
   }
   return RFM_OK;
+}
+
+}  // namespace
+
+rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda, cudaStream_t st,
+                                   double* scratch, long long scratch_len, unsigned int* sync, int* rank_flag_host) {
+  if (s < n || n <= 0) {
+    rfm_set_error("householder: need s >= n > 0");
+    return RFM_EINVAL;
+  }
+  if (scratch_len < rfm_householder_scratch(s, n)) {
+    rfm_set_error("householder: scratch too small");
+    return RFM_EINVAL;
+  }
+  RFM_TRY(qr_init_device());
+  const QrScratch q = carve(scratch, n);
+  RFM_CUDA(cudaMemsetAsync(sync + SYNC_BAR, 0, 2 * sizeof(unsigned int), st));
+  RFM_TRY(factor_range(A, s, lda, 0, n, n, st, q, sync));
+  return finish_r(A, n, lda, st, q, sync, rank_flag_host);
 }
 
 // ---------------------------------------------------------------------------
@@ -567,4 +596,211 @@ extern "C" rfm_status rfm_householder_r_noalloc(double* A_dev, int64_t s, int64_
   RFM_CUDA(cudaStreamSynchronize(st));
   if (rank_flag_host) *rank_flag_host = flag;
   return RFM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR with the trailing update on the tensor cores.
+//
+// Outer blocks of QB = 128 columns: inside a block the 32-wide panels and their
+// FP64 updates run as above; the block's reflectors V (rows x 128, unit
+// diagonal) then update the trailing matrix in compact-WY form
+//     W = V^T A_t,  W2 = T^T W,  A_t -= V W2
+// with both products on the emulated-FP64 tensor-core GEMM (digit splitting,
+// exact level accumulation).  T (128 x 128) comes from the FP64 Gram V^T V and
+// the reflector coefficients, T_jj = tau_j, T_{:j,j} = -tau_j T_{:j,:j} G_{:j,j}.
+
+rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, long long R, long long K, int ndig,
+                                int tile_rows, int* e, uint16_t* out, cudaStream_t st);
+rfm_status rfm_oz_slice_house_vt(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
+                                 int* e, uint16_t* out, cudaStream_t st);
+rfm_status rfm_oz_slice_house_v(const double* A, long long lda, long long j0, long long rows, long long nb, int ndig,
+                                int* e, uint16_t* out, cudaStream_t st);
+rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
+                       long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
+                       unsigned* err, cudaStream_t st);
+long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows);
+
+namespace {
+
+constexpr int QB = 128;
+constexpr int QDIG = 8;
+
+// Partial Gram of the block's reflectors over a slice of rows:
+// Gp[z][p][q] = sum_{r in slice z} v_p(r) v_q(r), p <= q.  256 threads, 8x8 each.
+__global__ void __launch_bounds__(256) k_gram_block(const double* __restrict__ A, long long lda, long long s,
+                                                    long long j0, int nbw, long long rchunk, double* __restrict__ Gp) {
+  __shared__ double Vs[32][QB + 1];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const long long rb = j0 + (long long)blockIdx.x * rchunk;
+  const long long re = min(s, rb + rchunk);
+  double acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+  for (long long r0 = rb; r0 < re; r0 += 32) {
+    for (int idx = tid; idx < 32 * QB; idx += 256) {
+      const int rr = idx & 31, p = idx >> 5;
+      const long long gr = r0 + rr;
+      Vs[rr][p] = (gr < re && p < nbw) ? vval(A, lda, j0, p, gr) : 0.0;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < 32; ++rr) {
+      double a[8], b[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        a[i] = Vs[rr][ty + 16 * i];
+        b[i] = Vs[rr][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  double* out = Gp + (size_t)blockIdx.x * QB * QB;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[(ty + 16 * i) * QB + tx + 16 * j] = acc[i][j];
+}
+
+// G = sum_z Gp[z] in a fixed order.
+__global__ void k_block_gsum(const double* __restrict__ Gp, int nz, double* __restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= QB * QB) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += Gp[(size_t)z * QB * QB + idx];
+  G[idx] = s;
+}
+
+// T from G and tau, column by column.  One CTA of QB threads; T is kept in
+// dynamic shared memory (QB x (QB+1) doubles).
+__global__ void k_block_t(const double* __restrict__ G, const double* __restrict__ tau, int nbw,
+                          double* __restrict__ T) {
+  extern __shared__ double Ts[];  // [QB][QB + 1]
+  for (int idx = threadIdx.x; idx < QB * (QB + 1); idx += blockDim.x) Ts[idx] = 0.0;
+  __syncthreads();
+  const int i = threadIdx.x;
+  for (int j = 0; j < nbw; ++j) {
+    const double tj = tau[j];
+    double v = 0.0;
+    if (i < j) {
+      for (int l = i; l < j; ++l) v += Ts[i * (QB + 1) + l] * G[l * QB + j];
+      v = -tj * v;
+    }
+    __syncthreads();
+    if (i < j) Ts[i * (QB + 1) + j] = v;
+    if (i == j) Ts[j * (QB + 1) + j] = tj;
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < QB * QB; idx += blockDim.x) T[idx] = Ts[(idx / QB) * (QB + 1) + idx % QB];
+}
+
+// W2[p + c*QB] = sum_{q <= p} T[q][p] W[q + c*QB]
+__global__ void k_block_wt(const double* __restrict__ T, const double* __restrict__ Wm, int nbw, long long nt,
+                           double* __restrict__ W2) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= nt) return;
+  const double* w = Wm + (size_t)c * QB;
+  double* o = W2 + (size_t)c * QB;
+  for (int p = 0; p < QB; ++p) {
+    double s = 0.0;
+    if (p < nbw)
+      for (int q = 0; q <= p; ++q) s += __ldg(T + q * QB + p) * w[q];  // T reads are warp-uniform
+    o[p] = s;
+  }
+}
+
+}  // namespace
+
+long long rfm_householder_emulated_bytes(long long s, long long n) {
+  const long long nzg = 152;
+  long long b = 0;
+  b += rfm_oz_digit_bytes(QB, s, QDIG, 128);  // V^T
+  b += rfm_oz_digit_bytes(n, s, QDIG, 64);    // A_t
+  b += rfm_oz_digit_bytes(s, QB, QDIG, 128);  // V
+  b += rfm_oz_digit_bytes(n, QB, QDIG, 64);   // W2
+  b += 8LL * (2LL * QB * n + nzg * QB * QB + 3LL * QB * QB);
+  b += 4LL * (QB + n + s + n) + 4096;
+  return b;
+}
+
+rfm_status rfm_householder_emulated(double* A, long long s, long long n, long long lda, cudaStream_t st,
+                                    double* scratch, long long scratch_len, unsigned int* sync, void* emu,
+                                    long long emu_bytes, int* rank_flag_host) {
+  if (s < n || n <= 0) {
+    rfm_set_error("householder: need s >= n > 0");
+    return RFM_EINVAL;
+  }
+  if (scratch_len < rfm_householder_scratch(s, n) || emu_bytes < rfm_householder_emulated_bytes(s, n)) {
+    rfm_set_error("householder: scratch too small");
+    return RFM_EINVAL;
+  }
+  RFM_TRY(qr_init_device());
+  static bool t_attr = false;
+  if (!t_attr) {
+    RFM_CUDA(cudaFuncSetAttribute(k_block_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(QB * (QB + 1) * sizeof(double))));
+    t_attr = true;
+  }
+  const QrScratch q = carve(scratch, n);
+  char* w = static_cast<char*>(emu);
+  auto take = [&](long long bytes) {
+    char* r = w;
+    w += (bytes + 255) & ~255LL;
+    return r;
+  };
+  uint16_t* d_vt = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(QB, s, QDIG, 128)));
+  uint16_t* d_at = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(n, s, QDIG, 64)));
+  uint16_t* d_v = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(s, QB, QDIG, 128)));
+  uint16_t* d_w2 = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(n, QB, QDIG, 64)));
+  double* Wm = reinterpret_cast<double*>(take(8LL * QB * n));
+  double* W2 = reinterpret_cast<double*>(take(8LL * QB * n));
+  double* Gp = reinterpret_cast<double*>(take(8LL * 152 * QB * QB));
+  double* T = reinterpret_cast<double*>(take(8LL * QB * QB));
+  double* Gs = reinterpret_cast<double*>(take(8LL * QB * QB));
+  int* e_vt = reinterpret_cast<int*>(take(4LL * QB));
+  int* e_at = reinterpret_cast<int*>(take(4LL * n));
+  int* e_v = reinterpret_cast<int*>(take(4LL * s));
+  int* e_w2 = reinterpret_cast<int*>(take(4LL * n));
+  unsigned int* err = sync + SYNC_ERR;
+  RFM_CUDA(cudaMemsetAsync(sync + SYNC_BAR, 0, 2 * sizeof(unsigned int), st));
+  for (long long J0 = 0; J0 < n; J0 += QB) {
+    const long long c1 = std::min<long long>(n, J0 + QB);
+    const int nbw = (int)(c1 - J0);
+    const long long rows = s - J0;
+    const long long nt = n - c1;
+    RFM_TRY(factor_range(A, s, lda, J0, c1, c1, st, q, sync));
+    if (nt <= 0) break;
+    {
+      ProfScope ps(PF_QR_PANEL, st);
+      const long long nzg = std::min<long long>(152, (rows + 255) / 256);
+      const long long rchunk = (rows + nzg - 1) / nzg;
+      const long long nz = (rows + rchunk - 1) / rchunk;
+      k_gram_block<<<(unsigned)nz, 256, 0, st>>>(A, lda, s, J0, nbw, rchunk, Gp);
+      RFM_CHECK_LAUNCH();
+      k_block_gsum<<<(QB * QB + 255) / 256, 256, 0, st>>>(Gp, (int)nz, Gs);
+      RFM_CHECK_LAUNCH();
+      k_block_t<<<1, QB, QB * (QB + 1) * sizeof(double), st>>>(Gs, q.tau + J0, nbw, T);
+      RFM_CHECK_LAUNCH();
+    }
+    {
+      ProfScope ps(PF_QR_VTA, st);
+      RFM_TRY(rfm_oz_slice_house_vt(A, lda, J0, nbw, rows, QDIG, e_vt, d_vt, st));
+      RFM_TRY(rfm_oz_slice_strided(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, e_at, d_at, st));
+      RFM_TRY(rfm_oz_gemm(d_vt, QDIG, e_vt, d_at, QDIG, e_at, nbw, nt, rows, QDIG + 1, Wm, QB, 0, err, st));
+      k_block_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(T, Wm, nbw, nt, W2);
+      RFM_CHECK_LAUNCH();
+    }
+    {
+      ProfScope ps(PF_QR_UPDATE, st);
+      RFM_TRY(rfm_oz_slice_house_v(A, lda, J0, rows, nbw, QDIG, e_v, d_v, st));
+      RFM_TRY(rfm_oz_slice_strided(W2, QB, 1, nt, nbw, QDIG, 64, e_w2, d_w2, st));
+      RFM_TRY(rfm_oz_gemm(d_v, QDIG, e_v, d_w2, QDIG, e_w2, rows, nt, nbw, QDIG + 1, A + (size_t)c1 * lda + J0, lda,
+                          1, err, st));
+    }
+  }
+  return finish_r(A, n, lda, st, q, sync, rank_flag_host);
 }

@@ -69,6 +69,18 @@ struct rfm_problem {
   long long ldr = 0;
   bool have_r = false;
   int rank_flag = 0;
+  // tensor-core (emulated FP64) paths
+  int precision = 0;        // 0 FP64, 1 + tensor-core sketch, 2 + tensor-core QR update
+  std::vector<int> colptr_h;
+  uint16_t* sdig = nullptr;  // S digit tiles of all column blocks
+  long long sdig_bytes = 0;
+  uint16_t* jdig = nullptr;  // J digit tiles of one column block
+  long long jdig_bytes = 0;
+  int* oz_e = nullptr;       // exponents: [s] for S (all 3) then [W] for J
+  long long oz_e_cap = 0;
+  long long* oz_toff = nullptr;
+  void* qr_emu = nullptr;
+  long long qr_emu_bytes = 0;
   // scratch
   double* work = nullptr;   // general vectors
   long long work_cap = 0;
@@ -107,7 +119,8 @@ void rfm_count_launch();
 // ---- optional per-kernel-family timing (prof.cu) -----------------------------
 enum {
   PF_ASSEMBLE = 0, PF_RESIDUAL, PF_SKETCH_COUNT, PF_SKETCH_GEN, PF_SKETCH_GEMM, PF_QR_PANEL, PF_QR_VTA,
-  PF_QR_UPDATE, PF_TRSV, PF_JMV, PF_JTMV, PF_LS_PRE, PF_LS_EVAL, PF_VECTOR, PF_EVAL, RFM_PROF_FAMILIES
+  PF_QR_UPDATE, PF_TRSV, PF_JMV, PF_JTMV, PF_LS_PRE, PF_LS_EVAL, PF_VECTOR, PF_EVAL, PF_OZ_GEMM, PF_OZ_SLICE,
+  RFM_PROF_FAMILIES
 };
 void* rfm_prof_begin(int fam, cudaStream_t st);
 void rfm_prof_end(void* h, cudaStream_t st);
@@ -133,6 +146,17 @@ rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y);
 rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x);
 rfm_status rfm_launch_count_sketch(rfm_problem* p, long long s, int kJ);
 rfm_status rfm_launch_gauss_sketch(rfm_problem* p, long long s, int kJ);
+rfm_status rfm_launch_gauss_sketch_tc(rfm_problem* p, long long s, int kJ);
+rfm_status rfm_householder_emulated(double* A, long long s, long long n, long long lda, cudaStream_t st,
+                                    double* scratch, long long scratch_len, unsigned int* sync, void* emu,
+                                    long long emu_bytes, int* rank_flag_host);
+long long rfm_householder_emulated_bytes(long long s, long long n);
+rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* rows, long long K, long long m_int,
+                               int W, int ndig, int* e, uint16_t* out, cudaStream_t st);
+rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
+                       long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
+                       unsigned* err, cudaStream_t st);
+long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows);
 rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda,
                                    cudaStream_t st, double* scratch, long long scratch_len,
                                    unsigned int* sync, int* rank_flag_host);
@@ -179,6 +203,17 @@ __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int
   return true;
 }
 #endif
+
+// Byte offset of element (row r, column k < 64) of a K-major tile with 128-byte
+// rows in the 128-byte swizzle pattern (16-byte chunk c of row r stored at
+// chunk c ^ (r mod 8); 8-row groups 1024 bytes apart), 2-byte elements.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int rfm_swz128(int r, int k) {
+  const int chunk = k >> 3;
+  return (r >> 3) * 1024 + (r & 7) * 128 + (((chunk ^ (r & 7)) & 7) << 4) + ((k & 7) << 1);
+}
 
 #define RFM_SYNC_WORDS 4096
 // layout of p->sync

@@ -14,6 +14,10 @@
 // K = |rows(b)|, N = W, M = s.  Its algorithmic cost is 2 s nnz(J) flops.
 #include <math.h>
 
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "philox.cuh"
 #include "rfm_internal.cuh"
 
@@ -198,6 +202,51 @@ __global__ void __launch_bounds__(256) k_gauss_gemm(const uint16_t* __restrict__
   }
 }
 
+// Digit tiles of S for the split product (one digit per entry: d = rint(16 z),
+// so S = d * 2^(3 - 7) with exponent 3), for every column block b: tiles
+// [s/128][ktiles_b] starting at tile toff[b], K index = position in the block's
+// row list.  Threads run along K so each warp writes within 128-byte rows.
+__global__ void k_gauss_digits(long long s, long long totK, const int* __restrict__ colptr, int G,
+                               const int* __restrict__ colrows, const long long* __restrict__ toff, uint32_t kJ,
+                               uint32_t key0, uint32_t key1, uint16_t* __restrict__ out) {
+  const long long half = s / 2;
+  const long long total = half * totK;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long g = t % totK, q = t / totK;
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (colptr[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const long long k = g - colptr[b];
+    const long long kt_b = (colptr[b + 1] - colptr[b] + 63) / 64;
+    const unsigned i = (unsigned)colrows[g] & 0x7fffffffu;
+    uint32_t c[4] = {2u, i, (uint32_t)q, kJ};
+    philox4x32_10(c, key0, key1);
+    const double u1 = uniform53(c[0], c[1]);
+    const double u2 = uniform53(c[2], c[3]);
+    const double rad = sqrt(-2.0 * log(1.0 - u1));
+    const double th = 6.283185307179586 * u2;
+    const float d0 = (float)rint(16.0 * (rad * cos(th)));
+    const float d1 = (float)rint(16.0 * (rad * sin(th)));
+    const long long r = 2 * q;
+    const long long mt = r >> 7;
+    const int rr = (int)(r & 127);
+    const long long tile = toff[b] + mt * kt_b + (k >> 6);
+    uint16_t* base = out + (size_t)tile * (128 * 64);
+    const int k64 = (int)(k & 63);
+    base[rfm_swz128(rr, k64) >> 1] = (uint16_t)(__float_as_uint(d0) >> 16);
+    base[rfm_swz128(rr + 1, k64) >> 1] = (uint16_t)(__float_as_uint(d1) >> 16);
+  }
+}
+
+__global__ void k_fill_int(int* __restrict__ x, long long n, int v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
 }  // namespace
 
 rfm_status rfm_launch_count_sketch(rfm_problem* p, long long s, int kJ) {
@@ -235,5 +284,64 @@ rfm_status rfm_launch_gauss_sketch(rfm_problem* p, long long s, int kJ) {
   dim3 grid((unsigned)((s + 127) / 128), (unsigned)((p->W + 63) / 64), (unsigned)p->G);
   k_gauss_gemm<<<grid, 256, 0, p->stream>>>(p->Sg, s, p->Jp, p->Js, p->colptr, p->colrows, p->m_int, p->W, p->B);
   RFM_CHECK_LAUNCH();
+  return RFM_OK;
+}
+
+// B[:, block b] = S[:, rows(b)] J[rows(b), block b] with the product emulated to
+// FP64 accuracy on the bf16 tensor cores: S is one exact digit per entry,
+// each Jacobian column block is split into 8 digits.
+rfm_status rfm_launch_gauss_sketch_tc(rfm_problem* p, long long s, int kJ) {
+  const uint32_t k0 = (uint32_t)(p->desc.seed & 0xffffffffull), k1 = (uint32_t)(p->desc.seed >> 32);
+  const int G = p->G;
+  const long long mtiles = (s + 127) / 128;
+  std::vector<long long> toff(G + 1, 0);
+  long long maxK = 0;
+  for (int b = 0; b < G; ++b) {
+    const long long K = p->colptr_h[b + 1] - p->colptr_h[b];
+    maxK = std::max(maxK, K);
+    toff[b + 1] = toff[b] + mtiles * ((K + 63) / 64);
+  }
+  const long long sbytes = toff[G] * 128 * 64 * 2;
+  const long long jbytes = rfm_oz_digit_bytes(p->W, maxK, 8, 64);
+  auto grow = [&](void** ptr, long long* cap, long long need) -> rfm_status {
+    if (need <= *cap) return RFM_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc(ptr, (size_t)need) != cudaSuccess) {
+      rfm_set_error("tensor-core sketch: allocation of " + std::to_string(need) + " bytes failed");
+      return RFM_ENOMEM;
+    }
+    *cap = need;
+    return RFM_OK;
+  };
+  RFM_TRY(grow((void**)&p->sdig, &p->sdig_bytes, sbytes));
+  RFM_TRY(grow((void**)&p->jdig, &p->jdig_bytes, jbytes));
+  RFM_TRY(grow((void**)&p->oz_e, &p->oz_e_cap, (s + p->W + 64) * (long long)sizeof(int)));
+  if (!p->oz_toff) {
+    if (cudaMalloc(&p->oz_toff, (size_t)(G + 1) * sizeof(long long)) != cudaSuccess) return RFM_ENOMEM;
+  }
+  RFM_CUDA(cudaMemcpyAsync(p->oz_toff, toff.data(), (G + 1) * sizeof(long long), cudaMemcpyHostToDevice, p->stream));
+  int* es = p->oz_e;
+  int* ej = p->oz_e + s;
+  {
+    ProfScope ps(PF_SKETCH_GEN, p->stream);
+    RFM_CUDA(cudaMemsetAsync(p->sdig, 0, (size_t)sbytes, p->stream));
+    const long long totK = p->colptr_h[G];
+    k_gauss_digits<<<152 * 16, 256, 0, p->stream>>>(s, totK, p->colptr, G, p->colrows, p->oz_toff, (uint32_t)kJ, k0, k1,
+                                                   p->sdig);
+    RFM_CHECK_LAUNCH();
+    k_fill_int<<<64, 256, 0, p->stream>>>(es, s, 3);
+    RFM_CHECK_LAUNCH();
+  }
+  ProfScope ps(PF_SKETCH_GEMM, p->stream);
+  for (int b = 0; b < G; ++b) {
+    const long long K = p->colptr_h[b + 1] - p->colptr_h[b];
+    if (K == 0) continue;
+    RFM_TRY(rfm_oz_slice_jblock(p->Jp, p->Js, p->colrows + p->colptr_h[b], K, p->m_int, p->W, 8, ej, p->jdig,
+                                p->stream));
+    RFM_TRY(rfm_oz_gemm(p->sdig + (size_t)toff[b] * 128 * 64, 1, es, p->jdig, 8, ej, s, p->W, K, 9,
+                        p->B + (size_t)b * p->W * s, s, 0, p->sync + SYNC_ERR, p->stream));
+  }
   return RFM_OK;
 }

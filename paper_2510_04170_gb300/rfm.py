@@ -17,7 +17,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ERANK", "ENONFINI
 EXPORTS = ["rfm_default_opts", "rfm_last_error", "rfm_problem_create", "rfm_problem_destroy", "rfm_problem_sizes",
            "rfm_get_features", "rfm_get_points", "rfm_assemble", "rfm_get_jacobian", "rfm_residual", "rfm_sketch",
            "rfm_qr", "rfm_set_r", "rfm_householder_r", "rfm_jmv", "rfm_trsv", "rfm_lsqr", "rfm_linesearch",
-           "rfm_ipn_solve", "rfm_amipn_solve", "rfm_eval"]
+           "rfm_ipn_solve", "rfm_amipn_solve", "rfm_eval", "rfm_set_precision",
+           "rfm_householder_r_tc", "rfm_emulated_dgemm"]
 
 
 class RfmError(RuntimeError):
@@ -86,6 +87,9 @@ def load(path=LIB_PATH):
         "rfm_ipn_solve": (I, [P, ctypes.POINTER(SolveOpts), VP, ctypes.POINTER(SolveInfo)]),
         "rfm_amipn_solve": (I, [P, ctypes.POINTER(SolveOpts), VP, ctypes.POINTER(SolveInfo)]),
         "rfm_eval": (I, [P, VP, VP, I64, VP]),
+        "rfm_set_precision": (I, [P, I]),
+        "rfm_householder_r_tc": (I, [VP, I64, I64, VP, VP, ctypes.POINTER(I)]),
+        "rfm_emulated_dgemm": (I, [VP, I64, VP, I64, VP, I64, I64, I64, I64, I, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +208,9 @@ class Problem:
         return F, nv.value
 
     # -- A4/A5: sketch and QR
+    def rfm_set_precision(self, precision):
+        _check(load().rfm_set_precision(self._h, precision))
+
     def rfm_sketch(self, kind, s, kJ, copy_out=True):
         B = self._dev(self.n, s) if copy_out else None
         _check(load().rfm_sketch(self._h, SKETCH[kind], s, kJ, _ptr(B)))
@@ -269,3 +276,22 @@ def rfm_householder_r(A_colmajor, s, n, stream=None):
     flag = ctypes.c_int()
     _check(load().rfm_householder_r(_ptr(A_colmajor), s, n, _stream(stream), _ptr(R), ctypes.byref(flag)))
     return R, bool(flag.value)
+
+
+def rfm_householder_r_tc(A_colmajor, s, n, stream=None):
+    """Tensor-core (emulated FP64 trailing update) Householder R; A is (n, s)
+    row-major == s x n column-major and is overwritten."""
+    R = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    flag = ctypes.c_int()
+    _check(load().rfm_householder_r_tc(_ptr(A_colmajor), s, n, _stream(stream), _ptr(R), ctypes.byref(flag)))
+    return R, bool(flag.value)
+
+
+def rfm_emulated_dgemm(A, B, digits=8, stream=None):
+    """C = A B for CUDA float64 matrices given column-major as tensors of
+    shape (K, M) and (N, K) (row-major transposes); returns C as (N, M)."""
+    K, M = A.shape
+    N = B.shape[0]
+    C = torch.empty(N, M, dtype=torch.float64, device="cuda")
+    _check(load().rfm_emulated_dgemm(_ptr(A), M, _ptr(B), K, _ptr(C), M, M, N, K, digits, _stream(stream)))
+    return C
