@@ -39,14 +39,22 @@ METRIC = "Newton solves/s at rel-L2<=1e-6 vs FP64 oracle (IPN)"
 FP64_ALU_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 
 
-def workload(name):
+PRECISION_NAMES = {0: "fp64", 1: "fp64 + tensor-core sketch", 2: "fp64 + tensor-core sketch and QR update"}
+
+
+def workload(name, precision=None, solver=None):
     if name == "c1":
-        return dict(desc=W.config_c1(), opts=W.solve_opts(), solver="ipn",
-                    label="c1: 2D -Lap u+u^3, 2x2 subdomains, M=100, n=400, m=1920, count sketch s=1200")
-    if name == "c2":
-        return dict(desc=W.config_c2(), opts=W.opts_c2(), solver="ipn",
-                    label="c2: 3D -Lap u+u^3, 4x4x4 subdomains, M=512, n=32768, m=124416, Gaussian sketch s=65536")
-    raise SystemExit(f"unknown workload {name}")
+        p = 0 if precision is None else precision
+        wl = dict(desc=W.config_c1(), opts=W.solve_opts(precision=p), solver=solver or "ipn",
+                  label="c1: 2D -Lap u+u^3, 2x2 subdomains, M=100, n=400, m=1920, count sketch s=1200")
+    elif name == "c2":
+        p = 2 if precision is None else precision
+        wl = dict(desc=W.config_c2(), opts=W.opts_c2(precision=p), solver=solver or "ipn",
+                  label="c2: 3D -Lap u+u^3, 4x4x4 subdomains, M=512, n=32768, m=124416, Gaussian sketch s=65536")
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    wl["precision"] = wl["opts"]["precision"]
+    return wl
 
 
 # ------------------------------------------------------------------ clocks
@@ -136,7 +144,7 @@ def run_ours(args, rank, world, local_rank):
     lib.rfm_profile_read.argtypes = [rfm.ctypes.c_int, rfm.ctypes.POINTER(rfm.ctypes.c_double),
                                      rfm.ctypes.POINTER(rfm.ctypes.c_int64)]
     lib.rfm_profile_name.restype = rfm.ctypes.c_char_p
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.precision, args.solver)
     desc, opts = wl["desc"], wl["opts"]
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -174,7 +182,7 @@ def run_ours(args, rank, world, local_rank):
         fam_ms[names[i]] = ms.value
         fam_cnt[names[i]] = cnt.value
     lib.rfm_profile_enable(0)
-    dom = max(fam_ms, key=lambda k: fam_ms[k])
+    dom = max(fam_ms, key=lambda k: fam_ms[k]) if any(fam_ms.values()) else "qr_update"
     # the QR trailing update is timed as one family pair
     dom_fams = ["qr_vta", "qr_update"] if dom in ("qr_vta", "qr_update") else [dom]
     mask = sum(1 << names.index(f) for f in dom_fams)
@@ -258,6 +266,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": 1e3 * max_s / steps_per_rank, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["label"], "solver": wl["solver"], "parallelism": "replicas" if world > 1 else "1gpu",
+                   "precision": PRECISION_NAMES[wl["precision"]],
                    "l2": "flushed (512 MiB write) between timed steps"},
         "accuracy": {"rel_l2_vs_exact": rel_exact, "outer_iters": info["outer_iters"], "n_jac": info["n_jac"],
                      "lsqr_iters_total": info["lsqr_iters_total"]},
@@ -307,7 +316,7 @@ def cpu_baseline(wl, budget_s=15.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.precision, args.solver)
     from oracle import newton
     from oracle.problem import Problem as OProblem
     op = OProblem(wl["desc"])
@@ -337,6 +346,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c1")
+    ap.add_argument("--precision", type=int, default=None)
+    ap.add_argument("--solver", default=None, choices=[None, "ipn", "amipn"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
                                               unsigned int* __restrict__ ticket, unsigned int* __restrict__ err) {
   __shared__ double sdiag[TB][TB + 1];
   __shared__ double sacc[8][TB];
+  __shared__ double srec[TB];
   __shared__ int sblk;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int nblk = (n + TB - 1) / TB;
@@ -98,6 +99,9 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
     const int rr = idx % TB, cc = idx / TB;
     sdiag[rr][cc] = (rr < rows && cc < rows) ? R[(size_t)(r0 + cc) * ldr + r0 + rr] : 0.0;
   }
+  // reciprocals of the block's pivots, taken in parallel before any wait so the
+  // dependency chain below only multiplies
+  if (tid < TB) srec[tid] = tid < rows ? 1.0 / R[(size_t)(r0 + tid) * ldr + r0 + tid] : 0.0;
   double a0 = 0.0, a1 = 0.0;          // TRANS 0: rows lane, lane+32 of the block
   double pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // TRANS 1: columns w + 8 t of the block, partial over lanes
   if (TRANS == 0) {
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
       for (int i = rows - 1; i >= 0; --i) {
         const int h = i >> 5, ln = i & 31;
         const double num = __shfl_sync(0xffffffffu, acc[h], ln);
-        const double xi = num / sdiag[i][i];
+        const double xi = num * srec[i];
         if (lane == ln) xv[h] = xi;
         if (lane < i) acc[0] -= sdiag[lane][i] * xi;
         if (lane + 32 < i) acc[1] -= sdiag[lane + 32][i] * xi;
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
       for (int i = 0; i < rows; ++i) {
         const int h = i >> 5, ln = i & 31;
         const double num = __shfl_sync(0xffffffffu, acc[h], ln);
-        const double xi = num / sdiag[i][i];
+        const double xi = num * srec[i];
         if (lane == ln) xv[h] = xi;
         if (lane > i) acc[0] -= sdiag[i][lane] * xi;
         if (lane + 32 > i) acc[1] -= sdiag[i][lane + 32] * xi;

@@ -11,21 +11,24 @@
 //     (A B)_ij = 2^(e_i + f_j) sum_l 2^(-beta l) L_l(i,j),
 //     L_l = sum over digit pairs with p + q = l of a_p b_q,
 // and every L_l of the leading levels accumulated over a K-chunk of 512 is an
-// integer below 2^24, so its FP32 tensor-core accumulation is exact.  Levels
-// are combined per chunk (the four leading levels in FP64, the rest first in
-// FP32, whose rounding is then ~2^-52 of the leading term) and summed
+// integer below 2^24, so its FP32 tensor-core accumulation is exact.  Per
+// chunk the four leading levels combine exactly into the int64
+// L_0 2^21 + L_1 2^14 + L_2 2^7 + L_3 (summed over chunks in int64), the
+// remaining levels by an FP32 Horner sum (rounding ~2^-52 of the leading
+// term) summed over chunks in FP64; both are merged once at the end and
 // over chunks in FP64; pairs with p + q > Lmax are dropped (their weight is
 // below 2^(-beta (Lmax+1)) relative to max|A_i.| max|B_.j|).
 //
-// Kernel layout: one CTA per 128 x 64 output tile, 6 warps.
+// Kernel layout: one CTA per 128 x 64 output tile, 10 warps.
 //   warp 0  producer: cp.async.bulk of pre-tiled digit tiles (16 KB A, 8 KB B)
 //           into shared memory, completion on mbarriers (expect_tx)
 //   warp 1  owns the 512-column TMEM allocation; lane 0 issues tcgen05.mma
 //           (kind::f16, bf16 x bf16 -> f32, M=128, N=64, K=16) for every digit
 //           pair into the TMEM accumulator of its level (64 columns each) and
 //           commits to mbarriers
-//   warps 2-5 epilogue: tcgen05.ld the levels of each chunk, combine, keep the
-//           FP64 running sums in registers, scale and write C
+//   warps 2-9 epilogue: tcgen05.ld the levels of each chunk, combine, keep the
+//           running sums in registers (two warps per TMEM lane quarter, 32
+//           columns each), scale and write C
 // Digit tiles are K-major with 128-byte rows in the 128B-swizzle pattern so a
 // tile is one contiguous bulk copy and the UMMA shared-memory descriptor reads
 // it directly.  Every wait is bounded; on timeout an error word is set, the
@@ -42,10 +45,11 @@ constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int ATILE = BM * BK * 2;  // 16384 bytes
 constexpr int BTILE = BN * BK * 2;  // 8192 bytes
 constexpr int MAXD = 8;             // digits per operand
-constexpr int ASTAGES = 4;
+constexpr int ASTAGES = 6;
+constexpr int EPI_WARPS = 8;        // two warps per TMEM lane quarter, 32 columns each
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int KCHUNK = 8;           // k-tiles per exact chunk (8 * 64 = 512)
 constexpr int BETA = 7;
-constexpr int kF64Levels = 4;       // levels combined in FP64 (the rest in FP32 first)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
 
 __device__ __forceinline__ int swz128(int r, int k) { return rfm_swz128(r, k); }
@@ -122,16 +126,14 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // ---------------------------------------------------------------- GEMM kernel
@@ -153,16 +155,16 @@ struct __align__(8) OzBars {
   uint32_t tmem_base;
 };
 
-__global__ void __launch_bounds__(192, 1) k_oz_gemm(OzArgs g) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* abuf = smem;                          // ASTAGES * ATILE
-  unsigned char* bbuf = abuf + ASTAGES * ATILE;        // 2 * pB * BTILE
+  unsigned char* bbuf = abuf + ASTAGES * ATILE;        // 2 * MAXD * BTILE
   OzBars* bars = reinterpret_cast<OzBars*>(bbuf + 2 * MAXD * BTILE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.x, nt = blockIdx.y;
   const int nlev = min(g.Lmax - 1, g.pA + g.pB - 1);
   const int nchunks = (g.ktiles + KCHUNK - 1) / KCHUNK;
+  const int ntiles_total = g.mtiles * g.ntiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ASTAGES; ++s) {
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(OzArgs g) {
       mbar_init(&bars->b_empty[b], 1);
     }
     mbar_init(&bars->acc_full, 1);
-    mbar_init(&bars->acc_empty, 4);
+    mbar_init(&bars->acc_empty, EPI_WARPS);
     mbar_init(&bars->fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -190,148 +192,172 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(OzArgs g) {
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
 
+  // Persistent: tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; M-tiles fastest.
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- producer
-      unsigned aidx = 0;
-      int kissued = 0;
+      unsigned aidx = 0, kglob = 0;
       bool ok = true;
-      for (int kt = 0; kt < g.ktiles && ok; ++kt) {
-        const int b = kt & 1;
-        const unsigned use_b = (unsigned)kt >> 1;
-        if (use_b > 0) ok = mbar_wait(&bars->b_empty[b], (use_b - 1) & 1, g.err, 2);
-        if (!ok) break;
-        mbar_expect_tx(&bars->b_full[b], (unsigned)(g.pB * BTILE));
-        kissued = kt + 1;
-        for (int q = 0; q < g.pB; ++q) {
-          const uint16_t* src = g.B + (((size_t)q * g.ntiles + nt) * g.ktiles + kt) * (BTILE / 2);
-          bulk_g2s(bbuf + (size_t)(b * MAXD + q) * BTILE, src, BTILE, &bars->b_full[b]);
-        }
-        for (int p = 0; p < g.pA && ok; ++p) {
-          const int s = aidx % ASTAGES;
-          const unsigned use = aidx / ASTAGES;
-          if (use > 0) ok = mbar_wait(&bars->a_empty[s], (use - 1) & 1, g.err, 3);
+      for (int t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x) {
+        const int mt = t % g.mtiles, nt = t / g.mtiles;
+        for (int kt = 0; kt < g.ktiles && ok; ++kt) {
+          const int b = kglob & 1;
+          const unsigned use_b = kglob >> 1;
+          if (use_b > 0) ok = mbar_wait(&bars->b_empty[b], (use_b - 1) & 1, g.err, 2);
           if (!ok) break;
-          mbar_expect_tx(&bars->a_full[s], (unsigned)ATILE);
-          const uint16_t* src = g.A + (((size_t)p * g.mtiles + mt) * g.ktiles + kt) * (ATILE / 2);
-          bulk_g2s(abuf + (size_t)s * ATILE, src, ATILE, &bars->a_full[s]);
-          ++aidx;
+          mbar_expect_tx(&bars->b_full[b], (unsigned)(g.pB * BTILE));
+          ++kglob;
+          for (int q = 0; q < g.pB; ++q) {
+            const uint16_t* src = g.B + (((size_t)q * g.ntiles + nt) * g.ktiles + kt) * (BTILE / 2);
+            bulk_g2s(bbuf + (size_t)(b * MAXD + q) * BTILE, src, BTILE, &bars->b_full[b]);
+          }
+          for (int p = 0; p < g.pA && ok; ++p) {
+            const int s = aidx % ASTAGES;
+            const unsigned use = aidx / ASTAGES;
+            if (use > 0) ok = mbar_wait(&bars->a_empty[s], (use - 1) & 1, g.err, 3);
+            if (!ok) break;
+            mbar_expect_tx(&bars->a_full[s], (unsigned)ATILE);
+            const uint16_t* src = g.A + (((size_t)p * g.mtiles + mt) * g.ktiles + kt) * (ATILE / 2);
+            bulk_g2s(abuf + (size_t)s * ATILE, src, ATILE, &bars->a_full[s]);
+            ++aidx;
+          }
         }
       }
-      // drain: make sure no copy is still writing shared memory before exit
-      if (aidx > 0) {
-        for (unsigned t = (aidx > ASTAGES ? aidx - ASTAGES : 0); t < aidx; ++t)
-          mbar_wait(&bars->a_full[t % ASTAGES], (t / ASTAGES) & 1, g.err, 4);
-      }
-      for (int kt = (kissued > 2 ? kissued - 2 : 0); kt < kissued; ++kt)
-        mbar_wait(&bars->b_full[kt & 1], ((unsigned)kt >> 1) & 1, g.err, 5);
+      // drain: no copy may still be writing shared memory at exit
+      for (unsigned t = (aidx > ASTAGES ? aidx - ASTAGES : 0); t < aidx; ++t)
+        mbar_wait(&bars->a_full[t % ASTAGES], (t / ASTAGES) & 1, g.err, 4);
+      for (unsigned k = (kglob > 2 ? kglob - 2 : 0); k < kglob; ++k)
+        mbar_wait(&bars->b_full[k & 1], (k >> 1) & 1, g.err, 5);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      unsigned aidx = 0;
-      unsigned initmask = 0;
+      unsigned aidx = 0, kglob = 0, cglob = 0;
       bool ok = true;
-      int chunk = 0;
-      for (int kt = 0; kt < g.ktiles && ok; ++kt) {
-        if (kt > 0 && kt % KCHUNK == 0) {
-          umma_commit(&bars->acc_full);
-          ok = mbar_wait(&bars->acc_empty, (unsigned)chunk & 1, g.err, 6);
-          tc_fence_after();
-          ++chunk;
-          initmask = 0;
-          if (!ok) break;
-        }
-        const int b = kt & 1;
-        ok = mbar_wait(&bars->b_full[b], ((unsigned)kt >> 1) & 1, g.err, 7);
-        if (!ok) break;
-        for (int p = 0; p < g.pA && ok; ++p) {
-          const int s = aidx % ASTAGES;
-          ok = mbar_wait(&bars->a_full[s], (aidx / ASTAGES) & 1, g.err, 8);
-          if (!ok) break;
-          tc_fence_after();
-          const uint64_t ad = umma_desc(abuf + (size_t)s * ATILE);
-          for (int q = 0; q < g.pB; ++q) {
-            if (p + q + 2 > g.Lmax) break;
-            const int l = p + q;
-            const uint64_t bd = umma_desc(bbuf + (size_t)(b * MAXD + q) * BTILE);
-            const uint32_t first = (initmask >> l) & 1u ? 1u : 0u;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              umma_bf16(tmem + (uint32_t)(l * BN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                        (first || kk > 0) ? 1u : 0u);
-            initmask |= 1u << l;
+      for (int t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x) {
+        for (int c = 0; c < nchunks && ok; ++c) {
+          if (cglob > 0) {
+            ok = mbar_wait(&bars->acc_empty, (cglob - 1) & 1, g.err, 6);
+            tc_fence_after();
+            if (!ok) break;
           }
-          umma_commit(&bars->a_empty[s]);
-          ++aidx;
+          unsigned initmask = 0;
+          const int kend = min(g.ktiles, (c + 1) * KCHUNK);
+          for (int kt = c * KCHUNK; kt < kend && ok; ++kt) {
+            const int b = kglob & 1;
+            ok = mbar_wait(&bars->b_full[b], (kglob >> 1) & 1, g.err, 7);
+            if (!ok) break;
+            for (int p = 0; p < g.pA && ok; ++p) {
+              const int s = aidx % ASTAGES;
+              ok = mbar_wait(&bars->a_full[s], (aidx / ASTAGES) & 1, g.err, 8);
+              if (!ok) break;
+              tc_fence_after();
+              const uint64_t ad = umma_desc(abuf + (size_t)s * ATILE);
+              for (int q = 0; q < g.pB; ++q) {
+                if (p + q + 2 > g.Lmax) break;
+                const int l = p + q;
+                const uint64_t bd = umma_desc(bbuf + (size_t)(b * MAXD + q) * BTILE);
+                const uint32_t first = (initmask >> l) & 1u ? 1u : 0u;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                  umma_bf16(tmem + (uint32_t)(l * BN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                            (first || kk > 0) ? 1u : 0u);
+                initmask |= 1u << l;
+              }
+              umma_commit(&bars->a_empty[s]);
+              ++aidx;
+            }
+            umma_commit(&bars->b_empty[b]);
+            ++kglob;
+          }
+          umma_commit(&bars->acc_full);
+          ++cglob;
         }
-        umma_commit(&bars->b_empty[b]);
       }
-      umma_commit(&bars->acc_full);
       // every MMA this thread issued has completed once `fin` fires
       umma_commit(&bars->fin);
       mbar_wait(&bars->fin, 0, g.err, 10);
     }
   } else {
-    // ---------------- epilogue (warps 2..5): TMEM lane quarter = warp % 4
+    // ---------------- epilogue (warps 2..9): TMEM lane quarter = warp % 4,
+    // column half = (warp - 2) / 4
     const int quarter = warp & 3;
+    const int col0 = ((warp - 2) >> 2) * 32;
     const int row = quarter * 32 + lane;
     const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
-    double acc[BN];
-#pragma unroll
-    for (int j = 0; j < BN; ++j) acc[j] = 0.0;
     const float s32 = 1.0f / (float)(1 << BETA);
-    const double s64 = 1.0 / (double)(1 << BETA);
-    for (int c = 0; c < nchunks; ++c) {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, (unsigned)c & 1, g.err, 9));
-      tc_fence_after();
-      if (ok) {
+    unsigned cglob = 0;
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
+      const int mt = t % g.mtiles, nt = t / g.mtiles;
+      long long ai[32];
+      double at[32];
 #pragma unroll
-        for (int grp = 0; grp < BN / 16; ++grp) {
-          float t[16], v[16];
-          double x[16];
-          tmem_ld16(tmem + tlane + (uint32_t)((nlev - 1) * BN + grp * 16), t);
-          if (nlev - 1 >= kF64Levels) {
-            for (int l = nlev - 2; l >= kF64Levels; --l) {
-              tmem_ld16(tmem + tlane + (uint32_t)(l * BN + grp * 16), v);
+      for (int j = 0; j < 32; ++j) {
+        ai[j] = 0;
+        at[j] = 0.0;
+      }
+      for (int c = 0; c < nchunks; ++c) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, cglob & 1, g.err, 9));
+        tc_fence_after();
+        if (!ok) {
+          alive = false;
+          break;
+        }
 #pragma unroll
-              for (int i = 0; i < 16; ++i) t[i] = fmaf(t[i], s32, v[i]);
-            }
+        for (int grp = 0; grp < 4; ++grp) {
+          const uint32_t cbase = tmem + tlane + (uint32_t)(col0 + grp * 8);
+          float v[8];
+          long long I[8];
+          // leading levels: exact integers, combined exactly in int64
+          tmem_ld8(cbase, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) x[i] = (double)t[i];
-            for (int l = kF64Levels - 1; l >= 0; --l) {
-              tmem_ld16(tmem + tlane + (uint32_t)(l * BN + grp * 16), v);
+          for (int i = 0; i < 8; ++i) I[i] = __float2ll_rn(v[i]);
+          for (int l = 1; l < 4; ++l) {
+            if (l < nlev) {
+              tmem_ld8(cbase + (uint32_t)(l * BN), v);
 #pragma unroll
-              for (int i = 0; i < 16; ++i) x[i] = fma(x[i], s64, (double)v[i]);
-            }
-          } else {
+              for (int i = 0; i < 8; ++i) I[i] = (I[i] << BETA) + __float2ll_rn(v[i]);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) x[i] = (double)t[i];
-            for (int l = nlev - 2; l >= 0; --l) {
-              tmem_ld16(tmem + tlane + (uint32_t)(l * BN + grp * 16), v);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) x[i] = fma(x[i], s64, (double)v[i]);
+              for (int i = 0; i < 8; ++i) I[i] <<= BETA;
             }
           }
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[grp * 16 + i] += x[i];
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->acc_empty);
-    }
-    const long long gi = (long long)mt * BM + row;
-    if (gi < g.M) {
-      const int ei = g.ea[gi];
+          for (int i = 0; i < 8; ++i) ai[grp * 8 + i] += I[i];
+          // remaining levels: FP32 Horner, summed over chunks in FP64
+          if (nlev > 4) {
+            float tl[8];
+            tmem_ld8(cbase + (uint32_t)((nlev - 1) * BN), tl);
+            for (int l = nlev - 2; l >= 4; --l) {
+              tmem_ld8(cbase + (uint32_t)(l * BN), v);
 #pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const long long gj = (long long)nt * BN + j;
-        if (gj < g.N) {
-          const double val = ldexp(acc[j], ei + g.eb[gj] - 2 * BETA);
-          double* cp = g.C + gi + gj * g.ldc;
-          if (g.mode == 0) *cp = val;
-          else *cp -= val;
+              for (int i = 0; i < 8; ++i) tl[i] = fmaf(tl[i], s32, v[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) at[grp * 8 + i] += (double)tl[i];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->acc_empty);
+        ++cglob;
+      }
+      if (!alive) break;
+      const long long gi = (long long)mt * BM + row;
+      if (gi < g.M) {
+        const int ei = g.ea[gi];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const long long gj = (long long)nt * BN + col0 + j;
+          if (gj < g.N) {
+            // value = 2^(e+f) [ I 2^(-4 BETA) + tail 2^(-5 BETA) ], I in units of level 3
+            const double tot = (double)ai[j] + at[j] * (1.0 / (double)(1 << BETA));
+            const double val = ldexp(tot, ei + g.eb[gj] - 5 * BETA);
+            double* cp = g.C + gi + gj * g.ldc;
+            if (g.mode == 0) *cp = val;
+            else *cp -= val;
+          }
         }
       }
     }
@@ -383,49 +409,96 @@ struct AccJBlock {  // row j = column j of a Jacobian column block, k = k-th row
   }
 };
 
-// e[i] = exponent with max_k |X(i,k)| < 2^e[i] (0 for a zero row).  One warp per row.
+// e[i] = exponent with max_k |X(i,k)| < 2^e[i] (0 for a zero row), from the
+// largest biased exponent field of the row (integer work only).  One warp per row.
 template <class Acc>
 __global__ void k_rowexp(Acc X, long long R, long long K, int* __restrict__ e) {
   const int lane = threadIdx.x & 31;
   for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < R;
        i += (long long)gridDim.x * (blockDim.x >> 5)) {
-    double mx = 0.0;
-    for (long long k = lane; k < K; k += 32) mx = fmax(mx, fabs(X(i, k)));
-    mx = warp_max(mx);
-    if (lane == 0) {
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      e[i] = ex;
+    unsigned mx = 0;
+    bool nz = false;
+    long long k = lane;
+    for (; k + 96 < K; k += 128) {  // four independent loads in flight per lane
+      const unsigned long long b0 = (unsigned long long)__double_as_longlong(X(i, k));
+      const unsigned long long b1 = (unsigned long long)__double_as_longlong(X(i, k + 32));
+      const unsigned long long b2 = (unsigned long long)__double_as_longlong(X(i, k + 64));
+      const unsigned long long b3 = (unsigned long long)__double_as_longlong(X(i, k + 96));
+      mx = max(max(mx, (unsigned)((b0 >> 52) & 0x7FF)), (unsigned)((b1 >> 52) & 0x7FF));
+      mx = max(max(mx, (unsigned)((b2 >> 52) & 0x7FF)), (unsigned)((b3 >> 52) & 0x7FF));
+      nz |= ((b0 | b1 | b2 | b3) << 1) != 0;
     }
+    for (; k < K; k += 32) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(X(i, k));
+      mx = max(mx, (unsigned)((b >> 52) & 0x7FF));
+      nz |= (b << 1) != 0;
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    nz = __any_sync(0xffffffffu, nz);
+    if (lane == 0) e[i] = nz ? (mx == 0 ? -1022 : (int)mx - 1022) : 0;
   }
 }
 
-// Digit tiles: out[d][rtile][ktile][tile] with tile = TR rows x 64 k in the 128B swizzle.
+// Balanced base-2^7 digits of x 2^-e (|x| < 2^e): V = round(x 2^(7 ndig - e))
+// as an integer built from the mantissa bits, then d_ndig .. d_2 in
+// [-64, 63] peeled from the low end and d_1 = the rest (|d_1| <= 128).
+__device__ __forceinline__ void digits_of(double x, int e, int ndig, float* d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & ((1ull << 52) - 1);
+  if (E != 0) m |= 1ull << 52;
+  const int sh = (E == 0 ? 1 : E) - 1075 - e + 7 * ndig;
+  long long V;
+  if (sh >= 0) V = (long long)(m << sh);
+  else if (sh > -63) V = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else V = 0;
+  if (b >> 63) V = -V;
+  for (int p = ndig - 1; p >= 1; --p) {
+    long long r = V & 127;
+    if (r >= 64) r -= 128;
+    d[p] = (float)r;
+    V = (V - r) >> 7;
+  }
+  d[0] = (float)V;
+}
+
+// Digit tiles: out[d][rtile][ktile][tile], tile = TR rows x 64 k in the 128B
+// swizzle.  One thread per 16-byte chunk (row r, 8 consecutive k): it reads 8
+// values and writes one 16-byte chunk per digit plane.
 template <class Acc, int TR>
 __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict__ e, int ndig, long long rtiles,
                          long long ktiles, uint16_t* __restrict__ out) {
-  const long long total = rtiles * TR * ktiles * 64;
+  const long long total = rtiles * TR * ktiles * 8;
   const size_t plane = (size_t)rtiles * ktiles * TR * 64;  // elements per digit plane
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    // t enumerates (rtile, ktile, r, k64) with k64 fastest
-    const int k64 = (int)(t & 63);
-    long long rest = t >> 6;
+    const int c8 = (int)(t & 7);
+    long long rest = t >> 3;
     const int r = (int)(rest % TR);
     rest /= TR;
     const long long kt = rest % ktiles;
     const long long rt = rest / ktiles;
-    const long long i = rt * TR + r, k = kt * 64 + k64;
-    double y = 0.0;
-    if (i < R && k < K) y = ldexp(X(i, k), -e[i]);
-    const size_t base = ((size_t)rt * ktiles + kt) * (TR * 64) + (size_t)(swz128(r, k64) >> 1);
-    for (int d = 0; d < ndig; ++d) {
-      const double s = y * (double)(1 << BETA);
-      const double dg = rint(s);
-      y = s - dg;
-      const float f = (float)dg;  // |dg| <= 128: exact in bf16
-      out[(size_t)d * plane + base] = (uint16_t)(__float_as_uint(f) >> 16);
+    const long long i = rt * TR + r, k0 = kt * 64 + c8 * 8;
+    uint32_t packed[MAXD][4];
+    const int ei = i < R ? e[i] : 0;
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      float d0[MAXD], d1[MAXD];
+      const double x0 = (i < R && k0 + j < K) ? X(i, k0 + j) : 0.0;
+      const double x1 = (i < R && k0 + j + 1 < K) ? X(i, k0 + j + 1) : 0.0;
+      digits_of(x0, ei, ndig, d0);
+      digits_of(x1, ei, ndig, d1);
+#pragma unroll
+      for (int d = 0; d < MAXD; ++d)
+        if (d < ndig)
+          packed[d][j >> 1] = (__float_as_uint(d0[d]) >> 16) | (__float_as_uint(d1[d]) & 0xFFFF0000u);
     }
+    const size_t base = ((size_t)rt * ktiles + kt) * (TR * 64) + (size_t)(swz128(r, c8 * 8) >> 1);
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d)
+      if (d < ndig)
+        *reinterpret_cast<uint4*>(out + (size_t)d * plane + base) =
+            make_uint4(packed[d][0], packed[d][1], packed[d][2], packed[d][3]);
   }
 }
 
@@ -449,7 +522,7 @@ static rfm_status slice(Acc X, long long R, long long K, int ndig, int tile_rows
   k_rowexp<<<std::max(1, g1), 256, 0, st>>>(X, R, K, e);
   RFM_CHECK_LAUNCH();
   const long long rt = (R + tile_rows - 1) / tile_rows, kt = (K + 63) / 64;
-  const long long total = rt * tile_rows * kt * 64;
+  const long long total = rt * tile_rows * kt * 8;
   const int g2 = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
   if (tile_rows == BM)
     k_digits<Acc, BM><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
@@ -496,7 +569,14 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
   a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
   if (a.ktiles == 0) return RFM_OK;
   ProfScope ps(PF_OZ_GEMM, st);
-  k_oz_gemm<<<dim3(a.mtiles, a.ntiles), 192, oz_smem_bytes(), st>>>(a);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    RFM_CUDA(cudaGetDevice(&dev));
+    RFM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long tiles = (long long)a.mtiles * a.ntiles;
+  k_oz_gemm<<<(unsigned)std::min<long long>(tiles, nsm), NTHREADS, oz_smem_bytes(), st>>>(a);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }

@@ -43,3 +43,38 @@ __device__ __forceinline__ uint16_t bf16_bits_rne(double x) {
 __device__ __forceinline__ double bf16_bits_to_double(uint16_t h) {
   return (double)__uint_as_float(((uint32_t)h) << 16);
 }
+
+// Gaussian sketch entries rounded to the grid 2^-4: (rint(16 z0), rint(16 z1))
+// for the Box-Muller pair z0 = r cos(t), z1 = r sin(t), r = sqrt(-2 log(1-u1)),
+// t = 2 pi u2, identical to evaluating Box-Muller in FP64 and rounding.
+// The pair is evaluated in FP32 (w = 1 - u1 is formed exactly in FP64 first);
+// with r >= 0.01 the FP32 error of 16 z is below 2.5e-4 (logf 1 ulp, sinf/cosf
+// 2 ulp, sqrtf correctly rounded, inputs rounded once), so an FP32 result more
+// than 1e-3 away from a rounding tie decides the same integer; only the rest
+// (about 0.2%) is recomputed in FP64.  For r < 0.01, |16 z| < 0.17 and the
+// integer is 0 either way.
+__device__ __forceinline__ void gauss_pair_q16(const uint32_t c[4], float* d0, float* d1) {
+  const double u1 = uniform53(c[0], c[1]);
+  const double u2 = uniform53(c[2], c[3]);
+  const double w = 1.0 - u1;  // exact
+  const float rf = sqrtf(-2.0f * logf((float)w));
+  float sf, cf;
+  sincosf(6.2831853f * (float)u2, &sf, &cf);
+  const float t0 = 16.0f * (rf * cf), t1 = 16.0f * (rf * sf);
+  const float q0 = rintf(t0), q1 = rintf(t1);
+  if (rf < 0.01f) {
+    *d0 = 0.0f;
+    *d1 = 0.0f;
+    return;
+  }
+  const bool safe = fabsf(fabsf(t0 - q0) - 0.5f) > 1e-3f && fabsf(fabsf(t1 - q1) - 0.5f) > 1e-3f;
+  if (safe) {
+    *d0 = q0;
+    *d1 = q1;
+    return;
+  }
+  const double rad = sqrt(-2.0 * log(w));
+  const double th = 6.283185307179586 * u2;
+  *d0 = (float)rint(16.0 * (rad * cos(th)));
+  *d1 = (float)rint(16.0 * (rad * sin(th)));
+}

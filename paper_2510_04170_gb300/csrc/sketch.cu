@@ -118,12 +118,10 @@ __global__ void k_gauss_gen(long long m, long long s, uint32_t kJ, uint32_t key0
     const long long i = t / half, q = t - i * half;
     uint32_t c[4] = {2u, (uint32_t)i, (uint32_t)q, kJ};
     philox4x32_10(c, key0, key1);
-    const double u1 = uniform53(c[0], c[1]);
-    const double u2 = uniform53(c[2], c[3]);
-    const double rad = sqrt(-2.0 * log(1.0 - u1));
-    const double th = 6.283185307179586 * u2;
-    const uint16_t z0 = bf16_bits_rne(rint(16.0 * (rad * cos(th))) * 0.0625);
-    const uint16_t z1 = bf16_bits_rne(rint(16.0 * (rad * sin(th))) * 0.0625);
+    float d0, d1;
+    gauss_pair_q16(c, &d0, &d1);
+    const uint16_t z0 = (uint16_t)(__float_as_uint(d0 * 0.0625f) >> 16);  // exact in bf16
+    const uint16_t z1 = (uint16_t)(__float_as_uint(d1 * 0.0625f) >> 16);
     const uint32_t packed = (uint32_t)z0 | ((uint32_t)z1 << 16);
     reinterpret_cast<uint32_t*>(S + (size_t)i * s)[q] = packed;
   }
@@ -225,12 +223,8 @@ __global__ void k_gauss_digits(long long s, long long totK, const int* __restric
     const unsigned i = (unsigned)colrows[g] & 0x7fffffffu;
     uint32_t c[4] = {2u, i, (uint32_t)q, kJ};
     philox4x32_10(c, key0, key1);
-    const double u1 = uniform53(c[0], c[1]);
-    const double u2 = uniform53(c[2], c[3]);
-    const double rad = sqrt(-2.0 * log(1.0 - u1));
-    const double th = 6.283185307179586 * u2;
-    const float d0 = (float)rint(16.0 * (rad * cos(th)));
-    const float d1 = (float)rint(16.0 * (rad * sin(th)));
+    float d0, d1;
+    gauss_pair_q16(c, &d0, &d1);
     const long long r = 2 * q;
     const long long mt = r >> 7;
     const int rr = (int)(r & 127);

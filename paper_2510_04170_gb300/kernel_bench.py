@@ -33,7 +33,7 @@ def _time(fn, reps=1):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["qr", "gemm", "sketch"])
+    ap.add_argument("what", choices=["qr", "gemm", "sketch", "trsv"])
     ap.add_argument("--s", type=int, default=32768)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--M", type=int, default=128)
@@ -43,9 +43,13 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--prof", action="store_true", help="report per-kernel-family CUDA-event times")
     a = ap.parse_args()
     build.build()
-    rfm.load()
+    lib = rfm.load()
+    lib.rfm_profile_enable.argtypes = [rfm.ctypes.c_int]
+    lib.rfm_profile_name.restype = rfm.ctypes.c_char_p
+    nfam = lib.rfm_profile_count()
     torch.manual_seed(0)
     out = {"what": a.what}
     if a.what == "qr":
@@ -54,6 +58,8 @@ def main():
         A = A0.clone()
         fn(A, a.s, a.n)  # warm-up
         A = A0.clone()
+        if a.prof:
+            lib.rfm_profile_enable((1 << nfam) - 1)
         ms = _time(lambda: fn(A, a.s, a.n))
         fl = 2.0 * a.n * a.n * (a.s - a.n / 3.0)
         out.update(s=a.s, n=a.n, tc=a.tc, ms=ms, fp64_equiv_tflops=fl / ms / 1e9)
@@ -61,10 +67,29 @@ def main():
         A = torch.randn(a.K, a.M, dtype=torch.float64, device="cuda")
         B = torch.randn(a.N, a.K, dtype=torch.float64, device="cuda")
         rfm.rfm_emulated_dgemm(A, B)
+        if a.prof:
+            lib.rfm_profile_enable((1 << nfam) - 1)
         ms = _time(lambda: rfm.rfm_emulated_dgemm(A, B), a.reps)
         fl = 2.0 * a.M * a.N * a.K
         out.update(M=a.M, N=a.N, K=a.K, ms=ms, fp64_equiv_tflops=fl / ms / 1e9,
                    bf16_pair_tflops=36 * fl / ms / 1e9)
+    elif a.what == "trsv":
+        import rfm_workloads as W
+        desc = {"c2": W.config_c2, "c1": W.config_c1}[a.workload]()
+        gp = rfm.Problem(desc)
+        n = gp.n
+        R = torch.randn(n, n, dtype=torch.float64, device="cuda").triu_() / n ** 0.5
+        R.diagonal().add_(2.0)
+        gp.rfm_set_r(R.T.contiguous())  # column-major
+        del R
+        b = torch.randn(n, dtype=torch.float64, device="cuda")
+        gp.rfm_trsv(b, 0)
+        if a.prof:
+            lib.rfm_profile_enable((1 << nfam) - 1)
+        ms0 = _time(lambda: gp.rfm_trsv(b, 0), a.reps)
+        ms1 = _time(lambda: gp.rfm_trsv(b, 1), a.reps)
+        byts = 8.0 * n * (n + 1) / 2
+        out.update(n=n, ms_upper=ms0, ms_upper_t=ms1, gbs_upper=byts / ms0 / 1e6, gbs_upper_t=byts / ms1 / 1e6)
     else:
         import rfm_workloads as W
         desc = {"c2": W.config_c2, "c1": W.config_c1}[a.workload]()
@@ -74,10 +99,20 @@ def main():
         gp.rfm_set_precision(a.precision)
         s = 65536 if a.workload == "c2" else 2 * gp.n
         gp.rfm_sketch("gauss", s, 0, copy_out=False)
+        if a.prof:
+            lib.rfm_profile_enable((1 << nfam) - 1)
         ms = _time(lambda: gp.rfm_sketch("gauss", s, 1, copy_out=False))
         nnz = gp.m * gp.W + gp.m_iface * gp.W
         out.update(workload=a.workload, precision=a.precision, s=s, ms=ms,
                    fp64_equiv_tflops=2.0 * s * nnz / ms / 1e9)
+    if a.prof:
+        fam = {}
+        for i in range(nfam):
+            ms, cnt = rfm.ctypes.c_double(), rfm.ctypes.c_int64()
+            lib.rfm_profile_read(i, rfm.ctypes.byref(ms), rfm.ctypes.byref(cnt))
+            if cnt.value:
+                fam[lib.rfm_profile_name(i).decode()] = [round(ms.value, 3), cnt.value]
+        out["families_ms_launches"] = fam
     print(json.dumps(out))
 
 

@@ -213,10 +213,11 @@ def test_lsqr_direction(name):
     res = la.lsqr(mv, rmv, b, op.n, 1e-6, 1e-6, 1e8, 2 * op.n)
     do = la.solve_upper(R, res.x)
     assert itn == res.itn and istop == res.istop
-    # Each R^{-1} / R^{-T} solve carries a relative error ~ u kappa(R) whatever
-    # the summation order, so two FP64 implementations agree to that level.
-    kap = np.linalg.cond(R)
-    assert np.linalg.norm(J @ (host(d) - do)) <= 10 * 2.2e-16 * kap * np.linalg.norm(J @ do)
+    # The direction only has to agree well below the inner tolerance eta = 1e-6
+    # (Alg. 1 step 3): rounding differences of the two FP64 implementations,
+    # amplified by kappa(R) (~1e10 for C1) in the R solves and over the Krylov
+    # steps, must stay 10x below eta in the J-norm.
+    assert np.linalg.norm(J @ (host(d) - do)) <= 1e-7 * np.linalg.norm(J @ do)
 
 
 @pytest.mark.parametrize("name", ["2d_c1", "3d_small", "3d_grayscott"])
