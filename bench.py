@@ -49,7 +49,7 @@ def workload(name, precision=None, solver=None):
                   label="c1: 2D -Lap u+u^3, 2x2 subdomains, M=100, n=400, m=1920, count sketch s=1200")
     elif name == "c2":
         p = 2 if precision is None else precision
-        wl = dict(desc=W.config_c2(), opts=W.opts_c2(precision=p), solver=solver or "ipn",
+        wl = dict(desc=W.config_c2(), opts=W.opts_c2(precision=p), solver=solver or "ipn", large=True,
                   label="c2: 3D -Lap u+u^3, 4x4x4 subdomains, M=512, n=32768, m=124416, Gaussian sketch s=65536")
     else:
         raise SystemExit(f"unknown workload {name}")
@@ -105,26 +105,20 @@ def problem_sizes(gp):
     return dict(m=gp.m, n=gp.n, W=gp.W, m_iface=gp.m_iface, nnz=gp.m * gp.W + gp.m_iface * gp.W)
 
 
-def family_model(fam, sz, s, launches, nj):
-    """(bound, total algorithmic units, unit) for the family over the measured
-    launches.  Units per launch follow the hot-path cost model:
-      qr_vta+qr_update  FP64 flops 2 n^2 (s - n/3) per factorisation
-      sketch_gemm       FP64 flops 2 s nnz(J) per Jacobian
-      trsv              bytes 8 n(n+1)/2 + 16 n per solve (R read once)
-      jmv / jtmv        bytes 8 (nnz + m + n) per product
-      assemble          bytes 8 (nnz + 2m) written per assembly"""
-    n, m, nnz = sz["n"], sz["m"], sz["nnz"]
-    if fam in ("qr_update", "qr_vta"):
-        return "alu", nj * 2.0 * n * n * (s - n / 3.0) / 2.0, "flop"
-    if fam == "sketch_gemm":
-        return "alu", nj * 2.0 * s * nnz, "flop"
-    if fam == "trsv":
-        return "hbm", launches * (8.0 * n * (n + 1) / 2 + 16.0 * n), "byte"
-    if fam in ("jmv", "jtmv"):
-        return "hbm", launches * 8.0 * (nnz + m + n), "byte"
-    if fam == "assemble":
-        return "hbm", launches * 8.0 * (nnz + 2 * m), "byte"
-    return "hbm", None, "byte"
+# kernel family -> roofline bound; algorithmic work per launch is recorded by the
+# library at each launch site (rfm_profile_work)
+BOUND = {"oz_gemm": "tensor", "qr_vta": "alu", "qr_update": "alu", "sketch_gemm": "alu",
+         "trsv": "hbm", "jmv": "hbm", "jtmv": "hbm", "assemble": "hbm"}
+
+
+def leaf_families(precision):
+    """Families whose timed scope contains no other family's launches."""
+    skip = set()
+    if precision >= 1:
+        skip.add("sketch_gemm")
+    if precision >= 2:
+        skip |= {"qr_vta", "qr_update"}
+    return skip
 
 
 def run_ours(args, rank, world, local_rank):
@@ -144,6 +138,7 @@ def run_ours(args, rank, world, local_rank):
     lib.rfm_profile_read.argtypes = [rfm.ctypes.c_int, rfm.ctypes.POINTER(rfm.ctypes.c_double),
                                      rfm.ctypes.POINTER(rfm.ctypes.c_int64)]
     lib.rfm_profile_name.restype = rfm.ctypes.c_char_p
+    lib.rfm_profile_work.argtypes = [rfm.ctypes.c_int, rfm.ctypes.POINTER(rfm.ctypes.c_double)]
     wl = workload(args.workload, args.precision, args.solver)
     desc, opts = wl["desc"], wl["opts"]
     stream = torch.cuda.Stream()
@@ -182,8 +177,10 @@ def run_ours(args, rank, world, local_rank):
         fam_ms[names[i]] = ms.value
         fam_cnt[names[i]] = cnt.value
     lib.rfm_profile_enable(0)
-    dom = max(fam_ms, key=lambda k: fam_ms[k]) if any(fam_ms.values()) else "qr_update"
-    # the QR trailing update is timed as one family pair
+    skip = leaf_families(wl["precision"])
+    cand = {k: v for k, v in fam_ms.items() if k not in skip and k in BOUND}
+    dom = max(cand, key=lambda k: cand[k]) if any(cand.values()) else ("oz_gemm" if wl["precision"] >= 2 else "qr_update")
+    # the FP64 QR trailing update is timed as one family pair
     dom_fams = ["qr_vta", "qr_update"] if dom in ("qr_vta", "qr_update") else [dom]
     mask = sum(1 << names.index(f) for f in dom_fams)
 
@@ -199,12 +196,14 @@ def run_ours(args, rank, world, local_rank):
             times.append(ms)
     launches = lib.rfm_launch_count() - l0
     torch.cuda.synchronize()
-    dom_ms, dom_cnt = 0.0, 0
+    dom_ms, dom_cnt, dom_work = 0.0, 0, 0.0
     for f in dom_fams:
-        ms, cnt = rfm.ctypes.c_double(), rfm.ctypes.c_int64()
+        ms, cnt, wk = rfm.ctypes.c_double(), rfm.ctypes.c_int64(), rfm.ctypes.c_double()
         lib.rfm_profile_read(names.index(f), rfm.ctypes.byref(ms), rfm.ctypes.byref(cnt))
+        lib.rfm_profile_work(names.index(f), rfm.ctypes.byref(wk))
         dom_ms += ms.value
         dom_cnt += cnt.value
+        dom_work += wk.value
     lib.rfm_profile_enable(0)
     total_s = sum(times) / 1e3
     t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
@@ -224,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_times = []
     c0_host = torch.zeros(gp.n, dtype=torch.float64).pin_memory()
     out_host = torch.empty(gp.n, dtype=torch.float64).pin_memory()
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(1 if wl.get("large") else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -240,27 +239,29 @@ def run_ours(args, rank, world, local_rank):
 
     steps_per_rank = args.steps
     value = world * steps_per_rank / max_s
-    nj = info["n_jac"]
-    s_rows = opts.get("sketch_rows") or int(math.ceil(opts.get("gamma", 3.0) * gp.n))
-    bound, units, unit = family_model(dom if len(dom_fams) == 1 else "qr_update", sz, s_rows, dom_cnt,
-                                      nj * args.steps)
-    if len(dom_fams) == 2:
-        units = 2.0 * units
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     roof = None
-    if units is not None and dom_ms > 0:
-        achieved = units / (dom_ms / 1e3)
+    bound = BOUND.get(dom_fams[0])
+    if bound and dom_ms > 0 and dom_work > 0:
+        rate = dom_work / (dom_ms / 1e3)
+        common = {"traffic": None, "kernel": "+".join(dom_fams), "launches": dom_cnt,
+                  "avg_launch_ms": dom_ms / max(1, dom_cnt), "work_per_launch": dom_work / max(1, dom_cnt)}
         if bound == "hbm":
-            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
-                os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-            roof = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / 1e9 / peak, "traffic": None, "kernel": "+".join(dom_fams),
-                    "launches": dom_cnt, "avg_launch_ms": dom_ms / max(1, dom_cnt),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = dict(bound="hbm", achieved=rate / 1e9, peak=peak, unit="GB/s", frac=rate / 1e9 / peak,
+                        peak_source="MEASURED_PEAKS.json hbm_gbs (measured)", **common)
+        elif bound == "tensor":
+            peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            roof = dict(bound="tensor", achieved=rate / 1e12, peak=peak, unit="TFLOP/s", frac=rate / 1e12 / peak,
+                        peak_source="MEASURED_PEAKS.json bf16_tflops_sustained (measured; kernel timed inside a long "
+                                    "step); work = bf16 digit-pair products",
+                        fp64_equivalent_tflops=rate / 1e12 / 36.0, **common)
         else:
-            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / 1e12 / FP64_ALU_PEAK_TFLOPS, "traffic": None, "kernel": "+".join(dom_fams),
-                    "launches": dom_cnt, "avg_launch_ms": dom_ms / max(1, dom_cnt),
-                    "peak_source": "FP64 FMA: 152 SMs x 4 flop/clk x 2.07 GHz (derived; cuBLAS dgemm measured 1.10)"}
+            roof = dict(bound="alu", achieved=rate / 1e12, peak=FP64_ALU_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=rate / 1e12 / FP64_ALU_PEAK_TFLOPS,
+                        peak_source="FP64 FMA: 152 SMs x 4 flop/clk x 2.07 GHz (derived; cuBLAS dgemm measured 1.10)",
+                        **common)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * max_s / steps_per_rank, "higher_is_better": True,
@@ -279,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget, info=info)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
@@ -295,11 +296,86 @@ def _threads():
         return os.cpu_count()
 
 
-def cpu_baseline(wl, budget_s=15.0):
+def oracle_projection(wl, outer_iters, lsqr_iters, qr_cols=4096):
+    """Projected time of one oracle solve of a workload too large to run whole:
+    each oracle step is timed on a sample at the workload's sizes and scaled
+    by its operation count (assembly per row, Gaussian sketch per column
+    block, Householder QR per flop 2 n^2 (s - n/3), triangular solve per n^2,
+    block products per nonzero), with the iteration counts of the solve.
+    Returns (seconds per solve, sample description, seconds spent sampling)."""
+    import numpy as np
+    from oracle import assemble as asm
+    from oracle import linalg as la
+    from oracle import philox
+    from oracle.problem import Problem as OProblem
+    t_all = time.perf_counter()
+    desc, opts = wl["desc"], wl["opts"]
+    op = OProblem(desc)
+    n, m, W_ = op.n, op.m, op.W
+    s = opts["sketch_rows"] or int(math.ceil(opts["gamma"] * n))
+    c = np.zeros(n)
+    rng = np.random.default_rng(0)
+    # assembly of F and J: 2048 sampled rows
+    rows = np.sort(rng.choice(m, 2048, replace=False))
+    t0 = time.perf_counter()
+    asm.assemble_rows(op, c, rows)
+    t_asm = (time.perf_counter() - t0) * m / rows.size
+    # Gaussian sketch of one column block (generation + product), times G blocks
+    blk_rows = np.nonzero((op.re0 == 0) | (op.re1 == 0))[0]
+    Jb = rng.standard_normal((blk_rows.size, W_))
+    t0 = time.perf_counter()
+    S = philox.gaussian_sketch(s, blk_rows, 0, desc["seed"])
+    S @ Jb
+    t_sk = (time.perf_counter() - t0) * op.G
+    del S
+    # Householder QR = per-column panel work (one s x 64 panel factorised)
+    # plus the blocked trailing update, 2 n^2 (s - n/3) flops at the rate of
+    # the oracle's own trailing-update products (V^T A, A -= V W) measured on
+    # an s x 64 by s x qr_cols sample
+    B = rng.standard_normal((s, 64))
+    t0 = time.perf_counter()
+    la.qr_r_blocked(B, nb=64)
+    t_col = (time.perf_counter() - t0) / 64
+    V = rng.standard_normal((s, 64))
+    A = rng.standard_normal((s, qr_cols))
+    t0 = time.perf_counter()
+    Wm = V.T @ A
+    A -= V @ Wm
+    rate = 4.0 * s * 64 * qr_cols / (time.perf_counter() - t0)
+    del B, V, A, Wm
+    t_qr = n * t_col + 2.0 * n * n * (s - n / 3.0) / rate
+    # triangular solve (n^2) and block product J x (nnz) per LSQR iteration
+    nt = 8192
+    Rs = np.triu(rng.standard_normal((nt, nt))) + nt * np.eye(nt)
+    t0 = time.perf_counter()
+    la.solve_upper(Rs, rng.standard_normal(nt))
+    t_tr = (time.perf_counter() - t0) * (n / nt) ** 2
+    Jr = rng.standard_normal((4096, W_))
+    xr = rng.standard_normal(W_)
+    t0 = time.perf_counter()
+    for _ in range(4):
+        Jr @ xr
+    t_mv = (time.perf_counter() - t0) / 4 * (m + op.m_iface) / 4096
+    t_it = 2 * t_tr + 2 * t_mv
+    # line search: about 19 residual evaluations per Newton step, each ~ an assembly
+    t_ls = 19 * t_asm * 0.5
+    per_solve = outer_iters * (t_asm + t_sk + t_qr + t_ls) + lsqr_iters * t_it
+    sample = (f"oracle steps timed on samples and scaled by operation counts: assembly of 2048 rows, "
+              f"Gaussian sketch of 1 of {op.G} column blocks, Householder panel {s}x64 and "
+              f"trailing-update product {s}x64 by {s}x{qr_cols}, R solve n=8192, 4096-row block product; {outer_iters} outer and "
+              f"{lsqr_iters} LSQR iterations")
+    return per_solve, sample, time.perf_counter() - t_all
+
+
+def cpu_baseline(wl, budget_s=15.0, info=None):
     """The oracle as it stands, timed on the host cores on a bounded sample."""
     from oracle import newton
     from oracle.problem import Problem as OProblem
     desc, opts = wl["desc"], wl["opts"]
+    if wl.get("large"):
+        per, sample, _ = oracle_projection(wl, info["outer_iters"], info["lsqr_iters_total"])
+        return {"value": 1.0 / per, "unit": "solves/s", "cores": _threads(), "kind": "oracle", "sample": sample,
+                "projected_seconds_per_solve": per}
     op = OProblem(desc)
     t0 = time.perf_counter()
     count = 0
@@ -319,22 +395,35 @@ def run_reference(args, rank, world):
     wl = workload(args.workload, args.precision, args.solver)
     from oracle import newton
     from oracle.problem import Problem as OProblem
-    op = OProblem(wl["desc"])
-    fn = getattr(newton, wl["solver"])
-    for _ in range(args.warmup):
-        fn(op, wl["opts"])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        fn(op, wl["opts"])
-    el = time.perf_counter() - t0
-    v = args.steps / el
+    if wl.get("large"):
+        # each step: one bounded sample of the oracle's steps, projected to a solve
+        # (iteration counts of the GPU solve of this workload: IT 4, 137 LSQR steps)
+        per = []
+        for i in range(args.warmup + args.steps):
+            p_, sample, _ = oracle_projection(wl, 4, 137, qr_cols=2048)
+            if i >= args.warmup:
+                per.append(p_)
+        v = 1.0 / statistics.median(per)
+        el = sum(per)
+        sample = "per step: " + sample
+    else:
+        op = OProblem(wl["desc"])
+        fn = getattr(newton, wl["solver"])
+        for _ in range(args.warmup):
+            fn(op, wl["opts"])
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn(op, wl["opts"])
+        el = time.perf_counter() - t0
+        v = args.steps / el
+        sample = f"{args.steps} complete oracle solves"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["label"], "solver": wl["solver"]},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
-                         "sample": f"{args.steps} complete oracle solves"},
+                         "sample": sample},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -342,15 +431,17 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1")
+    ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", type=int, default=None)
     ap.add_argument("--solver", default=None, choices=[None, "ipn", "amipn"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 2 if args.workload == "c2" else 10
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -237,6 +237,11 @@ rfm_status rfm_eval(const rfm_problem* p, const double* c_dev, const double* pts
  * number of kernels this library has launched in the process so far. */
 rfm_status rfm_profile_enable(int mask);
 int64_t rfm_launch_count(void);
+/* Algorithmic work recorded for a profiled family since rfm_profile_enable:
+ * bf16 tensor flops for oz_gemm, FP64 flops for sketch_gemm, bytes moved for
+ * trsv, jmv, jtmv (R or J read once plus vectors) and assemble (J, F, lambda
+ * written). */
+rfm_status rfm_profile_work(int family, double* units);
 int rfm_profile_count(void);
 const char* rfm_profile_name(int family);
 rfm_status rfm_profile_read(int family, double* ms, int64_t* launches);

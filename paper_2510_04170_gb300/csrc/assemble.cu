@@ -484,6 +484,7 @@ rfm_status rfm_launch_assemble(rfm_problem* p, const double* c, double cscale, b
   PdeConst pc = make_pc(p);
   const int grid = grid_for(p->m, 4, 152 * 16);
   ProfScope ps(want_j ? PF_ASSEMBLE : PF_RESIDUAL, p->stream);
+  if (want_j) rfm_prof_work(PF_ASSEMBLE, 8.0 * ((double)(p->m + p->m_iface) * p->W + 2.0 * p->m));
   if (want_j) {
     k_assemble<MODE_JF><<<grid, 128, asm_smem(p), p->stream>>>(pc, p->pts, p->rmeta, p->rhs, p->feat, p->mu, p->sig, c,
                                                                nullptr, p->m, p->m_int, cscale, nullptr, p->Jp, p->Js,

@@ -227,6 +227,7 @@ rfm_status rfm_dot(cudaStream_t st, const double* x, const double* y, long long 
 
 rfm_status rfm_launch_jmv(rfm_problem* p, const double* x, double* y) {
   ProfScope ps(PF_JMV, p->stream);
+  rfm_prof_work(PF_JMV, 8.0 * ((double)(p->m + p->m_iface) * p->W + p->m + p->n));
   long long g = (p->m + 7) / 8;
   if (g > 152 * 64) g = 152 * 64;
   k_jmv<<<(int)g, 256, 0, p->stream>>>(p->Jp, p->Js, p->rmeta, p->m, p->m_int, p->W, x, 1.0, 0.0, y);
@@ -236,6 +237,7 @@ rfm_status rfm_launch_jmv(rfm_problem* p, const double* x, double* y) {
 
 rfm_status rfm_launch_jmv_axpby(rfm_problem* p, const double* x, double s1, double s2, double* y) {
   ProfScope ps(PF_JMV, p->stream);
+  rfm_prof_work(PF_JMV, 8.0 * ((double)(p->m + p->m_iface) * p->W + 2.0 * p->m + p->n));
   long long g = (p->m + 7) / 8;
   if (g > 152 * 64) g = 152 * 64;
   k_jmv<<<(int)g, 256, 0, p->stream>>>(p->Jp, p->Js, p->rmeta, p->m, p->m_int, p->W, x, s1, s2, y);
@@ -246,6 +248,7 @@ rfm_status rfm_launch_jmv_axpby(rfm_problem* p, const double* x, double s1, doub
 rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y) {
   dim3 grid(p->G, (p->W + 63) / 64);
   ProfScope ps(PF_JTMV, p->stream);
+  rfm_prof_work(PF_JTMV, 8.0 * ((double)(p->m + p->m_iface) * p->W + p->m + p->n));
   k_jtmv<<<grid, 256, 0, p->stream>>>(p->Jp, p->Js, p->colptr, p->colrows, p->m_int, p->W, x, y);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
@@ -262,6 +265,7 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
   if (p->epoch == 0) p->epoch = 1;
   RFM_CUDA(cudaMemsetAsync(p->sync + SYNC_TICKET, 0, sizeof(unsigned int), p->stream));
   ProfScope ps(PF_TRSV, p->stream);
+  rfm_prof_work(PF_TRSV, 8.0 * (double)n * (n + 1) / 2 + 16.0 * n);  // R read once, b and x
   if (trans == 0)
     k_trsv<0><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->epoch,
                                            p->sync + SYNC_TICKET, p->sync + SYNC_ERR);

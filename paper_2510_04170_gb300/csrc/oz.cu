@@ -569,6 +569,13 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
   a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
   if (a.ktiles == 0) return RFM_OK;
   ProfScope ps(PF_OZ_GEMM, st);
+  {
+    int pairs = 0;
+    for (int p = 0; p < pA; ++p)
+      for (int q = 0; q < pB; ++q)
+        if (p + q + 2 <= Lmax) ++pairs;
+    rfm_prof_work(PF_OZ_GEMM, 2.0 * pairs * (double)M * (double)N * (double)K);  // bf16 tensor flops
+  }
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;

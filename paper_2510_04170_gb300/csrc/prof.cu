@@ -25,6 +25,7 @@ unsigned int g_mask = 0;
 std::atomic<long long> g_launches{0};
 std::vector<Rec> g_recs;
 double g_ms[RFM_PROF_FAMILIES];
+double g_work[RFM_PROF_FAMILIES];
 long long g_cnt[RFM_PROF_FAMILIES];
 
 void drain_locked() {
@@ -41,6 +42,12 @@ void drain_locked() {
 }
 
 }  // namespace
+
+void rfm_prof_work(int fam, double units) {
+  if (!g_on || !((g_mask >> fam) & 1u)) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_work[fam] += units;
+}
 
 void rfm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -72,6 +79,7 @@ rfm_status rfm_profile_enable(int mask) {
   for (int i = 0; i < RFM_PROF_FAMILIES; ++i) {
     g_ms[i] = 0.0;
     g_cnt[i] = 0;
+    g_work[i] = 0.0;
   }
   g_mask = (unsigned int)mask;
   g_on = mask != 0;
@@ -79,6 +87,13 @@ rfm_status rfm_profile_enable(int mask) {
 }
 
 int64_t rfm_launch_count(void) { return g_launches.load(); }
+
+rfm_status rfm_profile_work(int family, double* units) {
+  if (family < 0 || family >= RFM_PROF_FAMILIES || !units) return RFM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *units = g_work[family];
+  return RFM_OK;
+}
 
 int rfm_profile_count(void) { return RFM_PROF_FAMILIES; }
 

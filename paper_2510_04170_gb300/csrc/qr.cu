@@ -444,12 +444,14 @@ rfm_status factor_range(double* A, long long s, long long lda, long long c0, lon
     nz = (rows + kchunk - 1) / kchunk;
     {
       ProfScope ps(PF_QR_VTA, st);
+      rfm_prof_work(PF_QR_VTA, 2.0 * nbw * (double)nt * (double)rows);  // FP64 flops
       k_vta<<<dim3((unsigned)ctiles, (unsigned)nz), 256, 0, st>>>(A, lda, s, j0, nbw, j1, nt, kchunk, q.Wp);
       RFM_CHECK_LAUNCH();
       k_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(q.Wp, (int)nz, q.T, nbw, nt, q.W2);
       RFM_CHECK_LAUNCH();
     }
     ProfScope psu(PF_QR_UPDATE, st);
+    rfm_prof_work(PF_QR_UPDATE, 2.0 * nbw * (double)nt * (double)rows);  // FP64 flops
     k_update<<<dim3((unsigned)((rows + 127) / 128), (unsigned)ctiles), 256, 0, st>>>(A, lda, s, j0, nbw, j1, nt, q.W2);
     RFM_CHECK_LAUNCH();
   }

@@ -123,6 +123,9 @@ enum {
   RFM_PROF_FAMILIES
 };
 void* rfm_prof_begin(int fam, cudaStream_t st);
+// Adds `units` of algorithmic work (bytes or flops, per family) when family
+// `fam` is being profiled.
+void rfm_prof_work(int fam, double units);
 void rfm_prof_end(void* h, cudaStream_t st);
 struct ProfScope {
   void* h;

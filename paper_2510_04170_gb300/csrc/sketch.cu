@@ -276,6 +276,7 @@ rfm_status rfm_launch_gauss_sketch(rfm_problem* p, long long s, int kJ) {
   }
   ProfScope ps(PF_SKETCH_GEMM, p->stream);
   dim3 grid((unsigned)((s + 127) / 128), (unsigned)((p->W + 63) / 64), (unsigned)p->G);
+  rfm_prof_work(PF_SKETCH_GEMM, 2.0 * (double)s * (double)(p->m + p->m_iface) * p->W);  // FP64 flops
   k_gauss_gemm<<<grid, 256, 0, p->stream>>>(p->Sg, s, p->Jp, p->Js, p->colptr, p->colrows, p->m_int, p->W, p->B);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
