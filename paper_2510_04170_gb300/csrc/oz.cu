@@ -19,16 +19,17 @@
 // over chunks in FP64; pairs with p + q > Lmax are dropped (their weight is
 // below 2^(-beta (Lmax+1)) relative to max|A_i.| max|B_.j|).
 //
-// Kernel layout: one CTA per 128 x 64 output tile, 10 warps.
+// Kernel layout: persistent, one CTA per SM looping over 128 x 64 output
+// tiles, 10 warps.
 //   warp 0  producer: cp.async.bulk of pre-tiled digit tiles (16 KB A, 8 KB B)
 //           into shared memory, completion on mbarriers (expect_tx)
 //   warp 1  owns the 512-column TMEM allocation; lane 0 issues tcgen05.mma
 //           (kind::f16, bf16 x bf16 -> f32, M=128, N=64, K=16) for every digit
 //           pair into the TMEM accumulator of its level (64 columns each) and
 //           commits to mbarriers
-//   warps 2-9 epilogue: tcgen05.ld the levels of each chunk, combine, keep the
-//           running sums in registers (two warps per TMEM lane quarter, 32
-//           columns each), scale and write C
+//   warps 2-9 epilogue: tcgen05.ld the levels of each chunk, combine, keep
+//           the running sums in registers (two warps per TMEM lane quarter,
+//           32 columns each), scale and write C
 // Digit tiles are K-major with 128-byte rows in the 128B-swizzle pattern so a
 // tile is one contiguous bulk copy and the UMMA shared-memory descriptor reads
 // it directly.  Every wait is bounded; on timeout an error word is set, the
@@ -47,6 +48,7 @@ constexpr int BTILE = BN * BK * 2;  // 8192 bytes
 constexpr int MAXD = 8;             // digits per operand
 constexpr int ASTAGES = 6;
 constexpr int EPI_WARPS = 8;        // two warps per TMEM lane quarter, 32 columns each
+constexpr int EPI_COLS = BN / (EPI_WARPS / 4);
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int KCHUNK = 8;           // k-tiles per exact chunk (8 * 64 = 512)
 constexpr int BETA = 7;
@@ -280,9 +282,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     }
   } else {
     // ---------------- epilogue (warps 2..9): TMEM lane quarter = warp % 4,
-    // column half = (warp - 2) / 4
+    // column slice = (warp - 2) / 4
     const int quarter = warp & 3;
-    const int col0 = ((warp - 2) >> 2) * 32;
+    const int col0 = ((warp - 2) >> 2) * EPI_COLS;
     const int row = quarter * 32 + lane;
     const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
     const float s32 = 1.0f / (float)(1 << BETA);
@@ -290,10 +292,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
       const int mt = t % g.mtiles, nt = t / g.mtiles;
-      long long ai[32];
-      double at[32];
+      long long ai[EPI_COLS];
+      double at[EPI_COLS];  // tail levels, one FP64 add per element per chunk
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < EPI_COLS; ++j) {
         ai[j] = 0;
         at[j] = 0.0;
       }
@@ -305,19 +307,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
           break;
         }
 #pragma unroll
-        for (int grp = 0; grp < 4; ++grp) {
+        for (int grp = 0; grp < EPI_COLS / 8; ++grp) {
           const uint32_t cbase = tmem + tlane + (uint32_t)(col0 + grp * 8);
           float v[8];
           long long I[8];
-          // leading levels: exact integers, combined exactly in int64
+          // leading levels: exact integers below 2^24 (32-bit conversions),
+          // combined exactly in int64
           tmem_ld8(cbase, v);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) I[i] = __float2ll_rn(v[i]);
+          for (int i = 0; i < 8; ++i) I[i] = (long long)__float2int_rn(v[i]);
           for (int l = 1; l < 4; ++l) {
             if (l < nlev) {
               tmem_ld8(cbase + (uint32_t)(l * BN), v);
 #pragma unroll
-              for (int i = 0; i < 8; ++i) I[i] = (I[i] << BETA) + __float2ll_rn(v[i]);
+              for (int i = 0; i < 8; ++i) I[i] = (I[i] << BETA) + (long long)__float2int_rn(v[i]);
             } else {
 #pragma unroll
               for (int i = 0; i < 8; ++i) I[i] <<= BETA;
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
       if (gi < g.M) {
         const int ei = g.ea[gi];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < EPI_COLS; ++j) {
           const long long gj = (long long)nt * BN + col0 + j;
           if (gj < g.N) {
             // value = 2^(e+f) [ I 2^(-4 BETA) + tail 2^(-5 BETA) ], I in units of level 3
