@@ -228,6 +228,55 @@ rfm_status rfm_amipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c
 rfm_status rfm_eval(const rfm_problem* p, const double* c_dev, const double* pts_dev, int64_t npts,
                     double* u_dev);
 
+/* ---- Learned warm start (an addition of this library; the paper starts
+ * Newton from a fixed guess): an MLP maps PDE parameters to an initial
+ * coefficient vector c_0 for rfm_ipn_solve / rfm_amipn_solve; c_0 = 0 remains
+ * the fallback and the final Newton residual judges the result.
+ * Network d_in -> H (tanh) -> H (tanh) -> d_out; inputs, weights and hidden
+ * activations rounded to bfloat16, products accumulated in FP32, FP32 master
+ * weights trained by Adam (beta 0.9/0.999, eps 1e-8).  Parameters are one flat
+ * FP32 buffer with blocks W1 [H][d_in], b1, W2 [H][H], b2, W3 [d_out][H], b3
+ * at the offsets rfm_mlp_params returns.  All pointers are device pointers
+ * unless named *_host; batches are row-major [batch][dim] FP32. */
+typedef struct rfm_mlp rfm_mlp;
+rfm_status rfm_mlp_create(int d_in, int hidden, int d_out, uint64_t seed, void* cuda_stream, rfm_mlp** out);
+rfm_status rfm_mlp_destroy(rfm_mlp* net);
+int64_t rfm_mlp_num_params(const rfm_mlp* net);
+/* Copies the master parameters out (dst_dev) and/or in (src_dev); offsets_host
+ * (6 entries, nullable) receives the block offsets. */
+rfm_status rfm_mlp_params(rfm_mlp* net, float* dst_dev, const float* src_dev, int64_t* offsets_host);
+rfm_status rfm_mlp_forward(rfm_mlp* net, const float* x_dev, int batch, float* y_dev);
+/* Gradient of L = (1/batch) sum_b (y_b - t_b)^T G (y_b - t_b) (G block diagonal
+ * with d_out/gblk blocks of gblk x gblk, FP32 [blocks][gblk][gblk]; G_dev NULL
+ * means G = I/d_out) into grad_dev [num_params]; loss_host receives L. */
+rfm_status rfm_mlp_gradient(rfm_mlp* net, const float* x_dev, const float* t_dev, int batch, const float* G_dev,
+                            int gblk, float* grad_dev, double* loss_host);
+/* `steps` full-batch Adam steps on the same loss; loss_host gets the last L. */
+rfm_status rfm_mlp_train(rfm_mlp* net, const float* x_dev, const float* t_dev, int batch, const float* G_dev, int gblk,
+                         int steps, float lr, double* loss_host);
+/* Per-subdomain Gram of the features at evaluation points (the metric above):
+ * G[e*fields+f] = (1/npts) sum over points of subdomain e of phi_{e,f} phi_{e,f}^T,
+ * FP32 [G*fields][M][M].  Points [npts][dim] must be grouped by owning
+ * subdomain; owner_start_host (G+1 entries) delimits the groups. */
+rfm_status rfm_feature_gram(const rfm_problem* p, const double* pts_dev, int64_t npts,
+                            const int64_t* owner_start_host, float* G_dev);
+
+/* Function-space basis for the warm start.  The N snapshot coefficient
+ * vectors C [N][n] (converged solutions of one problem geometry) are centred
+ * (mean_dev [n] receives cbar) and orthonormalised in the mean-square inner
+ * product of u = Phi c over the npts points pts_dev [npts][dim] by modified
+ * Gram-Schmidt with column pivoting (largest remaining norm first), stopping
+ * when that norm falls to tol times the first.  U_dev [N][n] receives the
+ * modes (first *rank_host rows), Z_dev [N][N] the coordinates: snapshot j is
+ * cbar + sum_{k<rank} Z[j][k] U[k] up to the truncation.  Scratch is
+ * allocated inside; runs on the problem's stream and synchronises. */
+rfm_status rfm_function_basis(const rfm_problem* p, const double* C_dev, int N, const double* pts_dev, int64_t npts,
+                              double tol, double* mean_dev, double* U_dev, double* Z_dev, int* rank_host);
+/* c_dev [batch][n] = mean_dev + scale * y_dev [batch][rank] U_dev [rank][n]
+ * (FP64 accumulation); synchronises cuda_stream. */
+rfm_status rfm_basis_combine(const double* mean_dev, const double* U_dev, int64_t n, int rank, const float* y_dev,
+                             int batch, double scale, double* c_dev, void* cuda_stream);
+
 /* Benchmark instrumentation (not part of the method).  rfm_profile_enable(mask)
  * clears the counters and records a CUDA event pair around every launch of
  * the kernel families whose bit is set in mask (0 disables), on the stream the

@@ -436,6 +436,35 @@ __global__ void k_eval(PdeConst pc, const double* __restrict__ feat, const doubl
   }
 }
 
+// Phi[q][col] = scale * phi_col(x_q) for the W = fields*M features of the
+// owning subdomain of point q (FP32 output).  One warp per point.
+__global__ void k_phi_values(PdeConst pc, const double* __restrict__ feat, const double* __restrict__ mu,
+                             const double* __restrict__ sig, const double* __restrict__ lo,
+                             const double* __restrict__ hi, int N0, int N1, int N2, const double* __restrict__ pts,
+                             long long npts, float scale, float* __restrict__ Phi) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const int Ns[3] = {N0, N1, N2};
+  for (long long q = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); q < npts; q += nwarps) {
+    double x[3] = {0, 0, 0};
+    int e = 0;
+    for (int b = 0; b < pc.d; ++b) {
+      x[b] = pts[q * pc.d + b];
+      int t = (int)floor((x[b] - lo[b]) / (hi[b] - lo[b]) * Ns[b]);
+      t = t < 0 ? 0 : (t > Ns[b] - 1 ? Ns[b] - 1 : t);
+      e = e * Ns[b] + t;
+    }
+    const RowGeo g = row_geo(mu, sig, e, x, pc.d);
+    for (int col = lane; col < pc.W; col += 32) {
+      const long long fb = (long long)e * pc.W + col;
+      const double4 kb = *reinterpret_cast<const double4*>(feat + 4 * fb);
+      double t, s1;
+      feature_at(kb, g, pc.d, t, s1);
+      Phi[(size_t)q * pc.W + col] = scale * (float)t;
+    }
+  }
+}
+
 PdeConst make_pc(const rfm_problem* p) {
   PdeConst pc;
   pc.kind = p->desc.pde_kind;
@@ -532,6 +561,16 @@ rfm_status rfm_launch_eval(const rfm_problem* p, const double* c, const double* 
   ProfScope ps(PF_EVAL, p->stream);
   k_eval<<<grid_for(npts, 8, 152 * 32), 256, 0, p->stream>>>(pc, p->feat, p->mu, p->sig, lo, hi, p->N[0], p->N[1],
                                                              p->N[2], c, pts, npts, u);
+  RFM_CHECK_LAUNCH();
+  return RFM_OK;
+}
+
+rfm_status rfm_launch_phi_values(const rfm_problem* p, const double* pts, long long npts, float scale, float* Phi) {
+  PdeConst pc = make_pc(p);
+  const double* lo = p->X + 3 * p->nmaxbp;
+  const double* hi = lo + 3;
+  k_phi_values<<<grid_for(npts, 8, 152 * 32), 256, 0, p->stream>>>(pc, p->feat, p->mu, p->sig, lo, hi, p->N[0],
+                                                                   p->N[1], p->N[2], pts, npts, scale, Phi);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }

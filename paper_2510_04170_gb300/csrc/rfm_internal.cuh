@@ -144,6 +144,7 @@ rfm_status rfm_launch_ls_eval(rfm_problem* p, const double* P0, const double* P1
                               const double* V, double alpha, double* out_dev);
 rfm_status rfm_launch_eval(const rfm_problem* p, const double* c, const double* pts, long long npts,
                            double* u);
+rfm_status rfm_launch_phi_values(const rfm_problem* p, const double* pts, long long npts, float scale, float* Phi);
 rfm_status rfm_launch_jmv(rfm_problem* p, const double* x, double* y);
 rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y);
 rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x);

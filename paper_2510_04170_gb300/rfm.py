@@ -18,7 +18,9 @@ EXPORTS = ["rfm_default_opts", "rfm_last_error", "rfm_problem_create", "rfm_prob
            "rfm_get_features", "rfm_get_points", "rfm_assemble", "rfm_get_jacobian", "rfm_residual", "rfm_sketch",
            "rfm_qr", "rfm_set_r", "rfm_householder_r", "rfm_jmv", "rfm_trsv", "rfm_lsqr", "rfm_linesearch",
            "rfm_ipn_solve", "rfm_amipn_solve", "rfm_eval", "rfm_set_precision",
-           "rfm_householder_r_tc", "rfm_emulated_dgemm"]
+           "rfm_householder_r_tc", "rfm_emulated_dgemm", "rfm_mlp_create", "rfm_mlp_destroy",
+           "rfm_mlp_num_params", "rfm_mlp_params", "rfm_mlp_forward", "rfm_mlp_gradient", "rfm_mlp_train",
+           "rfm_feature_gram", "rfm_function_basis", "rfm_basis_combine"]
 
 
 class RfmError(RuntimeError):
@@ -90,6 +92,16 @@ def load(path=LIB_PATH):
         "rfm_set_precision": (I, [P, I]),
         "rfm_householder_r_tc": (I, [VP, I64, I64, VP, VP, ctypes.POINTER(I)]),
         "rfm_emulated_dgemm": (I, [VP, I64, VP, I64, VP, I64, I64, I64, I64, I, VP]),
+        "rfm_mlp_create": (I, [I, I, I, ctypes.c_uint64, VP, ctypes.POINTER(P)]),
+        "rfm_mlp_destroy": (I, [P]),
+        "rfm_mlp_num_params": (I64, [P]),
+        "rfm_mlp_params": (I, [P, VP, VP, ctypes.POINTER(I64)]),
+        "rfm_mlp_forward": (I, [P, VP, I, VP]),
+        "rfm_mlp_gradient": (I, [P, VP, VP, I, VP, I, VP, ctypes.POINTER(D)]),
+        "rfm_mlp_train": (I, [P, VP, VP, I, VP, I, I, ctypes.c_float, ctypes.POINTER(D)]),
+        "rfm_feature_gram": (I, [P, VP, I64, ctypes.POINTER(I64), VP]),
+        "rfm_function_basis": (I, [P, VP, I, VP, I64, D, VP, VP, VP, ctypes.POINTER(I)]),
+        "rfm_basis_combine": (I, [VP, VP, I64, I, VP, I, D, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -108,8 +120,8 @@ def _check(st, ok=(RFM_OK,)):
 def _ptr(t):
     if t is None:
         return None
-    if not t.is_cuda or t.dtype not in (torch.float64, torch.int32) or not t.is_contiguous():
-        raise ValueError("expected a contiguous CUDA float64/int32 tensor")
+    if not t.is_cuda or t.dtype not in (torch.float64, torch.int32, torch.float32) or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float64/float32/int32 tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -295,3 +307,84 @@ def rfm_emulated_dgemm(A, B, digits=8, stream=None):
     C = torch.empty(N, M, dtype=torch.float64, device="cuda")
     _check(load().rfm_emulated_dgemm(_ptr(A), M, _ptr(B), K, _ptr(C), M, M, N, K, digits, _stream(stream)))
     return C
+
+
+class MLP:
+    """Warm-start network (rfm_mlp_*): d_in -> H -> H -> d_out, bf16 weights and
+    activations with FP32 accumulation and FP32 Adam master weights."""
+
+    def __init__(self, d_in, hidden, d_out, seed=1, stream=None):
+        self._h = ctypes.c_void_p()
+        self.d_in, self.hidden, self.d_out = d_in, hidden, d_out
+        _check(load().rfm_mlp_create(d_in, hidden, d_out, seed, _stream(stream), ctypes.byref(self._h)))
+        self.num_params = load().rfm_mlp_num_params(self._h)
+
+    def close(self):
+        if self._h:
+            load().rfm_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        offs = (ctypes.c_int64 * 6)()
+        _check(load().rfm_mlp_params(self._h, _ptr(out), None, offs))
+        return out, list(offs)
+
+    def set_params(self, flat):
+        _check(load().rfm_mlp_params(self._h, None, _ptr(flat.contiguous()), None))
+
+    def forward(self, x):
+        y = torch.empty(x.shape[0], self.d_out, dtype=torch.float32, device="cuda")
+        _check(load().rfm_mlp_forward(self._h, _ptr(x.contiguous()), x.shape[0], _ptr(y)))
+        return y
+
+    def gradient(self, x, t, G=None, gblk=0):
+        g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        _check(load().rfm_mlp_gradient(self._h, _ptr(x.contiguous()), _ptr(t.contiguous()), x.shape[0],
+                                       _ptr(G), gblk, _ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, x, t, steps, lr, G=None, gblk=0):
+        loss = ctypes.c_double()
+        _check(load().rfm_mlp_train(self._h, _ptr(x.contiguous()), _ptr(t.contiguous()), x.shape[0], _ptr(G), gblk,
+                                    steps, lr, ctypes.byref(loss)))
+        return loss.value
+
+
+def rfm_feature_gram(problem, pts, owner_start):
+    """Per-subdomain feature Gram at points grouped by owner (see rfm.h)."""
+    G = torch.empty(problem.G * problem.desc["fields"], problem.desc["M"], problem.desc["M"],
+                    dtype=torch.float32, device="cuda")
+    starts = (ctypes.c_int64 * len(owner_start))(*[int(v) for v in owner_start])
+    _check(load().rfm_feature_gram(problem._h, _ptr(pts.contiguous()), pts.shape[0], starts, _ptr(G)))
+    return G
+
+
+def rfm_function_basis(problem, C, pts, tol=1e-8):
+    """Centred snapshot basis orthonormal in u-space (see rfm.h).  C is a CUDA
+    float64 tensor [N][n]; returns (mean [n], U [rank][n], Z [N][rank])."""
+    N, n = C.shape
+    mean = torch.empty(n, dtype=torch.float64, device="cuda")
+    U = torch.empty(N, n, dtype=torch.float64, device="cuda")
+    Z = torch.empty(N, N, dtype=torch.float64, device="cuda")
+    rank = ctypes.c_int()
+    _check(load().rfm_function_basis(problem._h, _ptr(C.contiguous()), N, _ptr(pts.contiguous()), pts.shape[0], tol,
+                                     _ptr(mean), _ptr(U), _ptr(Z), ctypes.byref(rank)))
+    r = rank.value
+    return mean, U[:r].contiguous(), Z[:, :r].contiguous()
+
+
+def rfm_basis_combine(mean, U, y, scale=1.0, stream=None):
+    """c = mean + scale * y U for a batch y [batch][rank] (float32)."""
+    batch = y.shape[0]
+    c = torch.empty(batch, mean.shape[0], dtype=torch.float64, device="cuda")
+    _check(load().rfm_basis_combine(_ptr(mean), _ptr(U), mean.shape[0], U.shape[0], _ptr(y.contiguous()), batch,
+                                    scale, _ptr(c), _stream(stream)))
+    return c
