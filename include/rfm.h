@@ -228,6 +228,38 @@ rfm_status rfm_amipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c
 rfm_status rfm_eval(const rfm_problem* p, const double* c_dev, const double* pts_dev, int64_t npts,
                     double* u_dev);
 
+/* ---- Batched solves (an addition of this library: many independent
+ * instances of one PDE family, e.g. different subdomain grids, M and
+ * coefficients, solved concurrently on one GPU).
+ * rfm_batch_create builds `count` problems from descs[] and `streams` CUDA
+ * streams (1..64), each served by one host worker during a solve.
+ * rfm_batch_solve runs IPN (solver 0, Alg. 1) or AMIPN (solver 1, Alg. 2) on
+ * every instance, largest n^2 s first; c_dev[i] is instance i's coefficient
+ * vector (device, n_i doubles, initial guess in, solution out) and infos[i]
+ * its record.  opts->precision = -1 lets the autotuner choose each
+ * instance's QR configuration (tuned_precision_out[i], nullable, receives the
+ * choice); 0..2 fixes it for all.  After its solve an instance frees its
+ * sketch and QR buffers.  Returns the first hard error (with the instance in
+ * rfm_last_error), else RFM_ENOCONV if any instance hit its iteration cap,
+ * else RFM_OK.  Problems of a batch must not be used concurrently with its
+ * solve. */
+typedef struct rfm_batch rfm_batch;
+rfm_status rfm_batch_create(const rfm_problem_desc* descs, int count, int streams, rfm_batch** out);
+rfm_status rfm_batch_destroy(rfm_batch* b);
+int rfm_batch_size(const rfm_batch* b);
+rfm_problem* rfm_batch_problem(rfm_batch* b, int i);
+rfm_status rfm_batch_solve(rfm_batch* b, const rfm_solve_opts* opts, int solver, double* const* c_dev,
+                           rfm_solve_info* infos, int* tuned_precision_out);
+/* QR autotuner: times the first 128 columns of a seeded random s x n
+ * factorisation for the FP64 path (precision 0) and the tensor-core path
+ * (precision 2), each with the panel spread over all SMs and over half of
+ * them, and returns the fastest (cached per (s, n) for the process).
+ * ms4_out (nullable) receives the four probe times in ms in the order
+ * {FP64 all, FP64 half, TC all, TC half}.  Allocates a probe matrix of s*n
+ * doubles plus the QR buffers. */
+rfm_status rfm_autotune_qr(int64_t s, int64_t n, void* cuda_stream, int* precision_out, int* panel_cap_out,
+                           double* ms4_out);
+
 /* ---- Learned warm start (an addition of this library; the paper starts
  * Newton from a fixed guess): an MLP maps PDE parameters to an initial
  * coefficient vector c_0 for rfm_ipn_solve / rfm_amipn_solve; c_0 = 0 remains
@@ -276,6 +308,25 @@ rfm_status rfm_function_basis(const rfm_problem* p, const double* C_dev, int N, 
  * (FP64 accumulation); synchronises cuda_stream. */
 rfm_status rfm_basis_combine(const double* mean_dev, const double* U_dev, int64_t n, int rank, const float* y_dev,
                              int batch, double scale, double* c_dev, void* cuda_stream);
+
+/* Warm-start object: the function-space basis of N training solutions
+ * C_dev [N][n] (rfm_function_basis on the points pts_dev, tolerance tol), their
+ * PDE parameters params_dev [N][d_in] (FP64; inputs are standardised per
+ * dimension with the training mean and deviation), and a network
+ * d_in -> hidden -> hidden -> rank trained on the coordinates divided by their
+ * root mean square.  The network's loss is the mean square of the coordinate
+ * error, which is the mean square of the error of u_0 over the points since
+ * the modes are orthonormal there.  predict writes c_0 [batch][n] (FP64) for
+ * params [batch][d_in].  Device pointers; the problem's stream is used. */
+typedef struct rfm_warmstart rfm_warmstart;
+rfm_status rfm_warmstart_create(const rfm_problem* p, const double* C_dev, const double* params_dev, int N, int d_in,
+                                const double* pts_dev, int64_t npts, double tol, int hidden, uint64_t seed,
+                                rfm_warmstart** out);
+rfm_status rfm_warmstart_destroy(rfm_warmstart* w);
+int rfm_warmstart_rank(const rfm_warmstart* w);
+rfm_mlp* rfm_warmstart_network(rfm_warmstart* w);
+rfm_status rfm_warmstart_train(rfm_warmstart* w, int steps, float lr, double* loss_host);
+rfm_status rfm_warmstart_predict(rfm_warmstart* w, const double* params_dev, int batch, double* c_dev);
 
 /* Benchmark instrumentation (not part of the method).  rfm_profile_enable(mask)
  * clears the counters and records a CUDA event pair around every launch of

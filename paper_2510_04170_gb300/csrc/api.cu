@@ -12,14 +12,17 @@
 
 #include "rfm_internal.cuh"
 
-rfm_status rfm_launch_jmv_axpby(rfm_problem* p, const double* x, double s1, double s2, double* y);
+rfm_status rfm_launch_jmv_axpby(rfm_problem* p, const double* x, double s1, double s2, double* y,
+                                const double* s2dev = nullptr);
 
 namespace {
 
 thread_local std::string g_err;
 
 // ---------------------------------------------------------------- vector kernels
-__global__ void k_scale_by(double* __restrict__ x, long long n, const double* __restrict__ s, int inv) {
+__global__ void k_scale_by(double* __restrict__ x, long long n, const double* __restrict__ s, int inv,
+                           const int* __restrict__ skip = nullptr) {
+  if (skip && *skip) return;
   const double sv = s[0];
   if (sv == 0.0) return;
   const double f = inv ? 1.0 / sv : sv;
@@ -44,10 +47,72 @@ __global__ void k_sub(double* __restrict__ y, const double* __restrict__ a, cons
     y[i] = a[i] - b[i];
 }
 
+// ---------------------------------------------------------------- LSQR scalars
+// Paige-Saunders LSQR (Alg. 1 step 4 solves J R^{-1} y = -F with it) keeps
+// its scalar recurrences on the device: the norms land in sc[0] (beta, ||u||)
+// and sc[1] (alpha, ||v||); the state below carries the rest between
+// iterations, and the convergence flag *done makes the iteration's kernels
+// return at once, so a fixed chunk of iterations can be replayed as one graph.
+enum LsqrSlot {
+  LS_ALPHA, LS_RHOBAR, LS_PHIBAR, LS_SUMSQ, LS_DD, LS_NORMB, LS_ETA, LS_CONLIM, LS_LIMIT, LS_ITN, LS_ISTOP, LS_SLOTS
+};
+
+struct Rot {
+  double rho, c, s, theta, rhobar, phi, phibar;
+};
+
+// One plane rotation of the bidiagonal (beta, alpha the new norms).
+__device__ __forceinline__ Rot lsqr_rot(const double* st, const double* sc) {
+  Rot r;
+  const double beta = sc[0], alpha = sc[1];
+  r.rho = hypot(st[LS_RHOBAR], beta);
+  r.c = st[LS_RHOBAR] / r.rho;
+  r.s = beta / r.rho;
+  r.theta = r.s * alpha;
+  r.rhobar = -r.c * alpha;
+  r.phi = r.c * st[LS_PHIBAR];
+  r.phibar = r.s * st[LS_PHIBAR];
+  return r;
+}
+
+// After u_1 = b / beta_1 and v_1 = R^-T J^T u_1 / alpha_1: initial state; a
+// zero right-hand side or a zero first alpha ends LSQR with x = 0.
+__global__ void k_lsqr_init(double* __restrict__ st, const double* __restrict__ sc, double eta, double conlim,
+                            double limit, int* __restrict__ done) {
+  const double beta = sc[0], alpha = sc[1];
+  st[LS_ALPHA] = alpha;
+  st[LS_RHOBAR] = alpha;
+  st[LS_PHIBAR] = beta;
+  st[LS_SUMSQ] = 0.0;
+  st[LS_DD] = 0.0;
+  st[LS_NORMB] = beta;
+  st[LS_ETA] = eta;
+  st[LS_CONLIM] = conlim;
+  st[LS_LIMIT] = limit;
+  st[LS_ITN] = 0.0;
+  st[LS_ISTOP] = 7.0;
+  *done = (beta > 0.0 && alpha > 0.0 && limit > 0.0) ? 0 : 1;
+  if (!(beta > 0.0 && alpha > 0.0)) st[LS_ISTOP] = 0.0;
+}
+
+// y = a x + b y with b = bscale * bdev[0]
+__global__ void k_axpby_dev(double* __restrict__ y, const double* __restrict__ x, long long n, double a,
+                            const double* __restrict__ bdev, double bscale, const int* __restrict__ skip) {
+  if (*skip) return;
+  const double b = bscale * bdev[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
 // LSQR update with the old w: dk = w / rho; x += phi dk; w = v - (theta/rho) w;
-// partial sums of ||dk||^2 and ||x||^2 per block.
+// partial sums of ||dk||^2 and ||x||^2 per block.  Every block derives the
+// rotation from the same device scalars.
 __global__ void k_lsqr_update(double* __restrict__ x, double* __restrict__ w, const double* __restrict__ v, long long n,
-                              double rho, double phi, double theta, double* __restrict__ partial) {
+                              const double* __restrict__ lst, const double* __restrict__ sc,
+                              double* __restrict__ partial, const int* __restrict__ skip) {
+  if (*skip) return;
+  const Rot r = lsqr_rot(lst, sc);
+  const double rho = r.rho, phi = r.phi, theta = r.theta;
   double sd = 0.0, sx = 0.0;
   const double tr = theta / rho;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -78,7 +143,12 @@ __global__ void k_lsqr_update(double* __restrict__ x, double* __restrict__ w, co
   }
 }
 
-__global__ void k_finish2(const double* __restrict__ partial, int np, double* __restrict__ out) {
+// End of an LSQR iteration (one warp): reduces ||dk||^2 and ||x||^2, advances
+// the state and applies the stopping tests (istop 1: ||r|| small, 2: ||A^T r||
+// small, 3: cond(A) above conlim, 7: iteration limit).
+__global__ void k_lsqr_finish(const double* __restrict__ partial, int np, double* __restrict__ st,
+                              const double* __restrict__ sc, int* __restrict__ done) {
+  if (*done) return;
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) {
     a += partial[2 * i];
@@ -86,10 +156,27 @@ __global__ void k_finish2(const double* __restrict__ partial, int np, double* __
   }
   a = warp_sum(a);
   b = warp_sum(b);
-  if (threadIdx.x == 0) {
-    out[0] = a;
-    out[1] = b;
-  }
+  if (threadIdx.x != 0) return;
+  const Rot r = lsqr_rot(st, sc);
+  const double beta = sc[0], alpha = sc[1];
+  st[LS_SUMSQ] += st[LS_ALPHA] * st[LS_ALPHA] + beta * beta;  // ||B_k||_F^2: alpha_i with beta_{i+1}
+  st[LS_ALPHA] = alpha;
+  st[LS_RHOBAR] = r.rhobar;
+  st[LS_PHIBAR] = r.phibar;
+  st[LS_DD] += a;
+  st[LS_ITN] += 1.0;
+  const double eta = st[LS_ETA];
+  const double normx = sqrt(b);
+  const double normA = sqrt(st[LS_SUMSQ]);
+  const double condA = normA * sqrt(st[LS_DD]);
+  const double normr = r.phibar;
+  const double normar = r.phibar * alpha * fabs(r.c);
+  int istop = 7;
+  if (normr <= eta * st[LS_NORMB] + eta * normA * normx) istop = 1;
+  else if (normar <= eta * normA * normr) istop = 2;
+  else if (condA >= st[LS_CONLIM]) istop = 3;
+  st[LS_ISTOP] = (double)istop;
+  if (istop != 7 || st[LS_ITN] >= st[LS_LIMIT]) *done = 1;
 }
 
 __global__ void k_copy_r(const double* __restrict__ A, long long lda, long long n, double* __restrict__ R) {
@@ -287,17 +374,16 @@ rfm_status ensure_sketch(rfm_problem* p, long long s, int kind) {
   return RFM_OK;
 }
 
-double* g_qr_scratch = nullptr;
-long long g_qr_scratch_len = 0;
-
-rfm_status ensure_qr_scratch(long long s, long long n) {
+// FP64 panel scratch of the Householder QR, owned by the problem (problems on
+// different streams or host threads never share it).
+rfm_status ensure_qr_scratch(rfm_problem* p, long long s, long long n) {
   const long long need = rfm_householder_scratch(s, n);
-  if (need > g_qr_scratch_len) {
-    dfree(g_qr_scratch);
-    g_qr_scratch = nullptr;
-    g_qr_scratch_len = 0;
-    RFM_TRY(dalloc(&g_qr_scratch, (size_t)need));
-    g_qr_scratch_len = need;
+  if (need > p->qr_scratch_len) {
+    dfree(p->qr_scratch);
+    p->qr_scratch = nullptr;
+    p->qr_scratch_len = 0;
+    RFM_TRY(dalloc(&p->qr_scratch, (size_t)need));
+    p->qr_scratch_len = need;
   }
   return RFM_OK;
 }
@@ -317,7 +403,7 @@ rfm_status do_sketch(rfm_problem* p, int kind, long long s, int kJ) {
 }
 
 rfm_status do_qr(rfm_problem* p) {
-  RFM_TRY(ensure_qr_scratch(p->s, p->n));
+  RFM_TRY(ensure_qr_scratch(p, p->s, p->n));
   int flag = 0;
   if (p->precision >= 2) {
     const long long need = rfm_householder_emulated_bytes(p->s, p->n);
@@ -330,11 +416,12 @@ rfm_status do_qr(rfm_problem* p) {
       p->qr_emu = buf;
       p->qr_emu_bytes = need;
     }
-    RFM_TRY(rfm_householder_emulated(p->B, p->s, p->n, p->s, p->stream, g_qr_scratch, g_qr_scratch_len, p->sync,
-                                     p->qr_emu, p->qr_emu_bytes, &flag));
+    RFM_TRY(rfm_householder_emulated(p->B, p->s, p->n, p->s, p->stream, p->qr_scratch, p->qr_scratch_len, p->sync,
+                                     p->qr_emu, p->qr_emu_bytes, &flag, p->qr_panel_cap));
   } else {
     RFM_TRY(
-        rfm_householder_inplace(p->B, p->s, p->n, p->s, p->stream, g_qr_scratch, g_qr_scratch_len, p->sync, &flag));
+        rfm_householder_inplace(p->B, p->s, p->n, p->s, p->stream, p->qr_scratch, p->qr_scratch_len, p->sync, &flag,
+                                p->qr_panel_cap));
   }
   p->R = p->B;
   p->ldr = p->s;
@@ -348,6 +435,93 @@ struct LsqrOut {
   int itn, istop;
 };
 
+constexpr int kLsqrChunk = 16;  // iterations per replayed graph
+
+// One chunk of kLsqrChunk iterations, every kernel guarded by the done flag.
+rfm_status lsqr_chunk(rfm_problem* p, double* lst, int* done) {
+  const long long m = p->m, n = p->n;
+  cudaStream_t st = p->stream;
+  double* u = wv(p, WV_U);
+  double* v = wv(p, WV_V);
+  double* w = wv(p, WV_W);
+  double* x = wv(p, WV_X);
+  double* tn = wv(p, WV_TN);
+  double* tn2 = wv(p, WV_TN2);
+  double* sc = p->red + 1024;
+  for (int it = 0; it < kLsqrChunk; ++it) {
+    // beta u = J R^{-1} v - alpha u
+    RFM_TRY(rfm_launch_trsv(p, 0, v, tn));
+    RFM_TRY(rfm_launch_jmv_axpby(p, tn, 1.0, -1.0, u, lst + LS_ALPHA));
+    RFM_TRY(rfm_norm2(st, u, m, p->red, sc));
+    k_scale_by<<<vgrid(m), 256, 0, st>>>(u, m, sc, 1, done);
+    RFM_CHECK_LAUNCH();
+    // alpha v = R^{-T} J^T u - beta v
+    RFM_TRY(rfm_launch_jtmv(p, u, tn));
+    RFM_TRY(rfm_launch_trsv(p, 1, tn, tn2));
+    k_axpby_dev<<<vgrid(n), 256, 0, st>>>(v, tn2, n, 1.0, sc, -1.0, done);
+    RFM_CHECK_LAUNCH();
+    RFM_TRY(rfm_norm2(st, v, n, p->red, sc + 1));
+    k_scale_by<<<vgrid(n), 256, 0, st>>>(v, n, sc + 1, 1, done);
+    RFM_CHECK_LAUNCH();
+    k_lsqr_update<<<kVecBlocks, 256, 0, st>>>(x, w, v, n, lst, sc, p->red, done);
+    RFM_CHECK_LAUNCH();
+    k_lsqr_finish<<<1, 32, 0, st>>>(p->red, kVecBlocks, lst, sc, done);
+    RFM_CHECK_LAUNCH();
+  }
+  return RFM_OK;
+}
+
+void drop_lsqr_graph(rfm_problem* p) {
+  if (p->lsqr_graph) cudaGraphExecDestroy((cudaGraphExec_t)p->lsqr_graph);
+  p->lsqr_graph = nullptr;
+  p->lsqr_graph_key = 0;
+}
+
+// Captures one chunk into a graph (once per problem and preconditioner
+// storage), or rebuilds it when R moved.
+rfm_status lsqr_graph(rfm_problem* p, double* lst, int* done) {
+  // everything the captured launches bake in: R and the vector workspace
+  unsigned long long key = 1469598103934665603ull;
+  for (unsigned long long v : {(unsigned long long)(uintptr_t)p->R, (unsigned long long)p->ldr,
+                               (unsigned long long)(uintptr_t)p->work, (unsigned long long)p->work_cap,
+                               (unsigned long long)(uintptr_t)p->Jp, (unsigned long long)(uintptr_t)p->Js})
+    key = (key ^ v) * 1099511628211ull;
+  if (p->lsqr_graph && p->lsqr_graph_key == key) return RFM_OK;
+  drop_lsqr_graph(p);
+  // capture on a private stream (the problem's may be the legacy default
+  // stream, which cannot be captured); the graph is replayed on p->stream
+  if (!p->cap_stream) RFM_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  const long long before = rfm_launches_now();
+  cudaGraph_t g = nullptr;
+  cudaStream_t home = p->stream;
+  p->stream = p->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+  rfm_status r = e == cudaSuccess ? lsqr_chunk(p, lst, done) : RFM_ECUDA;
+  if (e == cudaSuccess) e = cudaStreamEndCapture(p->stream, &g);
+  p->stream = home;
+  const long long captured = rfm_launches_now() - before;
+  rfm_count_launches(-captured);  // captured, not run
+  if (r != RFM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) {
+    g_err = std::string("lsqr graph capture: ") + cudaGetErrorString(e);
+    return RFM_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    g_err = std::string("lsqr graph instantiate: ") + cudaGetErrorString(e);
+    return RFM_ECUDA;
+  }
+  p->lsqr_graph = ex;
+  p->lsqr_graph_key = key;
+  p->lsqr_graph_launches = captured;
+  return RFM_OK;
+}
+
 rfm_status lsqr(rfm_problem* p, const double* b, double eta, double conlim, long long iter_lim, double* d_out,
                 LsqrOut* out) {
   const long long m = p->m, n = p->n;
@@ -357,82 +531,63 @@ rfm_status lsqr(rfm_problem* p, const double* b, double eta, double conlim, long
   double* w = wv(p, WV_W);
   double* x = wv(p, WV_X);
   double* tn = wv(p, WV_TN);
-  double* tn2 = wv(p, WV_TN2);
   double* sc = p->red + 1024;  // device scalars
+  double* lst = p->red + 2048;  // LSQR state
+  int* done = (int*)(p->sync + SYNC_LSQR_DONE);
   out->itn = 0;
   out->istop = 0;
+  // u_1 = b / beta_1, v_1 = R^{-T} J^T u_1 / alpha_1, w_1 = v_1, x_0 = 0
   RFM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
   RFM_CUDA(cudaMemcpyAsync(u, b, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   RFM_TRY(rfm_norm2(st, u, m, p->red, sc));
-  double hs[2];
-  RFM_TRY(read_scalars(p, sc, 1, hs));
-  double beta = hs[0];
-  const double normb = beta;
-  if (!(beta > 0.0)) {
-    RFM_CUDA(cudaMemsetAsync(d_out, 0, n * sizeof(double), st));
-    return RFM_OK;
-  }
   k_scale_by<<<vgrid(m), 256, 0, st>>>(u, m, sc, 1);
   RFM_CHECK_LAUNCH();
   RFM_TRY(rfm_launch_jtmv(p, u, tn));
   RFM_TRY(rfm_launch_trsv(p, 1, tn, v));
   RFM_TRY(rfm_norm2(st, v, n, p->red, sc + 1));
-  RFM_TRY(read_scalars(p, sc + 1, 1, hs));
-  double alpha = hs[0];
-  if (!(alpha > 0.0)) {
-    RFM_CUDA(cudaMemsetAsync(d_out, 0, n * sizeof(double), st));
-    return RFM_OK;
-  }
   k_scale_by<<<vgrid(n), 256, 0, st>>>(v, n, sc + 1, 1);
   RFM_CHECK_LAUNCH();
   RFM_CUDA(cudaMemcpyAsync(w, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double phibar = beta, rhobar = alpha, sumsq = 0.0, dd = 0.0;
-  int itn = 0, istop = 7;
-  while (itn < iter_lim) {
-    ++itn;
-    // beta u = J R^{-1} v - alpha u
-    RFM_TRY(rfm_launch_trsv(p, 0, v, tn));
-    RFM_TRY(rfm_launch_jmv_axpby(p, tn, 1.0, -alpha, u));
-    RFM_TRY(rfm_norm2(st, u, m, p->red, sc));
-    k_scale_by<<<vgrid(m), 256, 0, st>>>(u, m, sc, 1);
-    RFM_CHECK_LAUNCH();
-    // alpha v = R^{-T} J^T u - beta v
-    RFM_TRY(rfm_launch_jtmv(p, u, tn));
-    RFM_TRY(rfm_launch_trsv(p, 1, tn, tn2));
-    RFM_TRY(read_scalars(p, sc, 1, hs));
-    beta = hs[0];
-    sumsq += alpha * alpha + beta * beta;  // ||B_k||_F^2: alpha_i with beta_{i+1}
-    k_axpby<<<vgrid(n), 256, 0, st>>>(v, tn2, n, 1.0, -beta);
-    RFM_CHECK_LAUNCH();
-    RFM_TRY(rfm_norm2(st, v, n, p->red, sc + 1));
-    k_scale_by<<<vgrid(n), 256, 0, st>>>(v, n, sc + 1, 1);
-    RFM_CHECK_LAUNCH();
-    RFM_TRY(read_scalars(p, sc + 1, 1, hs));
-    alpha = hs[0];
-    const double rho = hypot(rhobar, beta);
-    const double c = rhobar / rho, s = beta / rho;
-    const double theta = s * alpha;
-    rhobar = -c * alpha;
-    const double phi = c * phibar;
-    phibar = s * phibar;
-    k_lsqr_update<<<kVecBlocks, 256, 0, st>>>(x, w, v, n, rho, phi, theta, p->red);
-    RFM_CHECK_LAUNCH();
-    k_finish2<<<1, 32, 0, st>>>(p->red, kVecBlocks, sc + 2);
-    RFM_CHECK_LAUNCH();
-    RFM_TRY(read_scalars(p, sc + 2, 2, hs));
-    dd += hs[0];
-    const double normx = sqrt(hs[1]);
-    const double normA = sqrt(sumsq);
-    const double condA = normA * sqrt(dd);
-    const double normr = phibar;
-    const double normar = phibar * alpha * fabs(c);
-    if (normr <= eta * normb + eta * normA * normx) istop = 1;
-    else if (normar <= eta * normA * normr) istop = 2;
-    else if (condA >= conlim) istop = 3;
-    if (istop != 7) break;
+  k_lsqr_init<<<1, 1, 0, st>>>(lst, sc, eta, conlim, (double)iter_lim, done);
+  RFM_CHECK_LAUNCH();
+  // chunks of iterations until the device sets done; replayed from a graph
+  // unless per-kernel profiling is on (event timing needs eager launches)
+  const bool graph = !rfm_prof_active();
+  p->skip = done;
+  rfm_status r = RFM_OK;
+  if (graph) r = lsqr_graph(p, lst, done);
+  int* hflag = (int*)p->hostbuf;
+  for (long long chunks = 0; r == RFM_OK; ++chunks) {
+    if (graph) {
+      if (cudaGraphLaunch((cudaGraphExec_t)p->lsqr_graph, st) != cudaSuccess) {
+        g_err = "lsqr graph launch failed";
+        r = RFM_ECUDA;
+        break;
+      }
+      rfm_count_launches(p->lsqr_graph_launches);
+    } else {
+      r = lsqr_chunk(p, lst, done);
+      if (r != RFM_OK) break;
+    }
+    if (cudaMemcpyAsync(hflag, done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      g_err = "lsqr: CUDA error";
+      r = RFM_ECUDA;
+      break;
+    }
+    if (*hflag) break;
+    if (chunks * kLsqrChunk > iter_lim + kLsqrChunk) {  // the device stops at iter_lim; guard the host loop too
+      g_err = "lsqr: iteration limit not honoured";
+      r = RFM_ECUDA;
+      break;
+    }
   }
-  out->itn = itn;
-  out->istop = istop;
+  p->skip = nullptr;
+  RFM_TRY(r);
+  double hs[2];
+  RFM_TRY(read_scalars(p, lst + LS_ITN, 2, hs));
+  out->itn = (int)hs[0];
+  out->istop = (int)hs[1];
   RFM_TRY(rfm_launch_trsv(p, 0, x, d_out));
   return check_timeout(p);
 }
@@ -693,7 +848,9 @@ rfm_status rfm_problem_destroy(rfm_problem* p) {
   else cudaDeviceSynchronize();
   void* bufs[] = {p->X, p->mu, p->sig, p->feat, p->segs, p->pts, p->rmeta, p->rhs, p->Jp, p->Js, p->lam, p->F,
                   p->colptr, p->colrows, p->B, p->Sg, p->hbuck, p->hsign, p->bptr, p->brows, p->Rown, p->work,
-                  p->red, p->sync, p->sdig, p->jdig, p->oz_e, p->oz_toff, p->qr_emu};
+                  p->red, p->sync, p->sdig, p->jdig, p->oz_e, p->oz_toff, p->qr_emu, p->qr_scratch};
+  drop_lsqr_graph(p);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void* b : bufs) dfree(b);
   if (p->hostbuf) cudaFreeHost(p->hostbuf);
   delete p;
@@ -823,19 +980,23 @@ rfm_status rfm_householder_r(double* A_dev, int64_t s, int64_t n, void* cuda_str
     return RFM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  RFM_TRY(ensure_qr_scratch(s, n));
+  const long long qs = rfm_householder_scratch(s, n);
+  double* scratch = nullptr;
   unsigned int* sync = nullptr;
-  RFM_TRY(dalloc(&sync, RFM_SYNC_WORDS));
-  RFM_CUDA(cudaMemsetAsync(sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st));
+  RFM_TRY(dalloc(&scratch, (size_t)qs));
+  rfm_status r = dalloc(&sync, RFM_SYNC_WORDS);
   int flag = 0;
-  rfm_status r = rfm_householder_inplace(A_dev, s, n, s, st, g_qr_scratch, g_qr_scratch_len, sync, &flag);
+  if (r == RFM_OK && cudaMemsetAsync(sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st) != cudaSuccess) r = RFM_ECUDA;
+  if (r == RFM_OK) r = rfm_householder_inplace(A_dev, s, n, s, st, scratch, qs, sync, &flag);
   if (r == RFM_OK) {
     dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
     k_copy_r<<<grid, 256, 0, st>>>(A_dev, s, n, R_dev);
     RFM_CHECK_LAUNCH();
     if (cudaStreamSynchronize(st) != cudaSuccess) r = RFM_ECUDA;
   }
-  cudaFree(sync);
+  cudaStreamSynchronize(st);
+  dfree(sync);
+  dfree(scratch);
   if (rank_flag_host) *rank_flag_host = flag;
   return r;
 }
@@ -847,23 +1008,27 @@ rfm_status rfm_householder_r_tc(double* A_dev, int64_t s, int64_t n, void* cuda_
     return RFM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  RFM_TRY(ensure_qr_scratch(s, n));
+  const long long qs = rfm_householder_scratch(s, n);
+  double* scratch = nullptr;
   unsigned int* sync = nullptr;
   char* emu = nullptr;
   const long long eb = rfm_householder_emulated_bytes(s, n);
-  RFM_TRY(dalloc(&sync, RFM_SYNC_WORDS));
-  rfm_status r = dalloc(&emu, (size_t)eb);
+  RFM_TRY(dalloc(&scratch, (size_t)qs));
+  rfm_status r = dalloc(&sync, RFM_SYNC_WORDS);
+  if (r == RFM_OK) r = dalloc(&emu, (size_t)eb);
   int flag = 0;
   if (r == RFM_OK && cudaMemsetAsync(sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st) != cudaSuccess) r = RFM_ECUDA;
-  if (r == RFM_OK) r = rfm_householder_emulated(A_dev, s, n, s, st, g_qr_scratch, g_qr_scratch_len, sync, emu, eb, &flag);
+  if (r == RFM_OK) r = rfm_householder_emulated(A_dev, s, n, s, st, scratch, qs, sync, emu, eb, &flag);
   if (r == RFM_OK) {
     dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
     k_copy_r<<<grid, 256, 0, st>>>(A_dev, s, n, R_dev);
     rfm_count_launch();
     if (cudaStreamSynchronize(st) != cudaSuccess) r = RFM_ECUDA;
   }
-  cudaFree(sync);
-  if (emu) cudaFree(emu);
+  cudaStreamSynchronize(st);
+  dfree(sync);
+  dfree(emu);
+  dfree(scratch);
   if (rank_flag_host) *rank_flag_host = flag;
   return r;
 }

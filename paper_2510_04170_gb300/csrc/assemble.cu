@@ -497,14 +497,16 @@ rfm_status rfm_launch_setup(rfm_problem* p) {
   k_points<<<grid_for(p->m, 256, 1 << 30), 256, 0, p->stream>>>(
       p->segs, p->nseg, p->X, p->nmaxbp, pc, p->N[0], p->N[1], p->N[2], nullptr, p->pts, p->rmeta, p->rhs, p->m);
   RFM_CHECK_LAUNCH();
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const cudaError_t attr = [] {  // once, thread-safe
     const int bytes = 4 * 2 * RFM_MAX_WIDTH * (int)sizeof(double);
-    RFM_CUDA(cudaFuncSetAttribute(k_assemble<MODE_JF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    RFM_CUDA(cudaFuncSetAttribute(k_assemble<MODE_RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    RFM_CUDA(cudaFuncSetAttribute(k_assemble<MODE_LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    attr_set = true;
-  }
+    cudaError_t e = cudaFuncSetAttribute(k_assemble<MODE_JF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_assemble<MODE_RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_assemble<MODE_LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }();
+  RFM_CUDA(attr);
   return RFM_OK;
 }
 

@@ -24,7 +24,10 @@ constexpr int TB = 64;  // triangular block
 __global__ void __launch_bounds__(256) k_jmv(const double* __restrict__ Jp, const double* __restrict__ Js,
                                              const int4* __restrict__ meta, long long m, long long m_int, int W,
                                              const double* __restrict__ x, double s1, double s2,
+                                             const double* __restrict__ s2dev, const int* __restrict__ skip,
                                              double* __restrict__ y) {
+  if (skip && *skip) return;
+  if (s2dev) s2 *= s2dev[0];
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nwarps) {
@@ -46,7 +49,8 @@ __global__ void __launch_bounds__(256) k_jmv(const double* __restrict__ Jp, cons
 __global__ void __launch_bounds__(256) k_jtmv(const double* __restrict__ Jp, const double* __restrict__ Js,
                                               const int* __restrict__ colptr, const int* __restrict__ colrows,
                                               long long m_int, int W, const double* __restrict__ x,
-                                              double* __restrict__ y) {
+                                              const int* __restrict__ skip, double* __restrict__ y) {
+  if (skip && *skip) return;
   const int b = blockIdx.x;
   const int c0 = blockIdx.y * 64;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -78,8 +82,11 @@ __global__ void __launch_bounds__(256) k_jtmv(const double* __restrict__ Jp, con
 template <int TRANS>
 __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long long ldr, int n,
                                               const double* __restrict__ rhs, double* __restrict__ x,
-                                              unsigned int* __restrict__ flags, unsigned int epoch,
-                                              unsigned int* __restrict__ ticket, unsigned int* __restrict__ err) {
+                                              unsigned int* __restrict__ flags, const unsigned int* __restrict__ epoch_dev,
+                                              unsigned int* __restrict__ ticket, unsigned int* __restrict__ err,
+                                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const unsigned int epoch = *epoch_dev;  // set by k_trsv_prep, which ran before this launch
   __shared__ double sdiag[TB][TB + 1];
   __shared__ double sacc[8][TB];
   __shared__ double srec[TB];
@@ -181,6 +188,15 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
   }
 }
 
+// Next epoch for the block flags (never 0, the initial flag value) and a fresh
+// ticket counter; runs before every k_trsv so that replays of a captured graph
+// see a new epoch each time.
+__global__ void k_trsv_prep(unsigned int* __restrict__ epoch, unsigned int* __restrict__ ticket) {
+  unsigned int e = *epoch + 1u;
+  *epoch = e == 0u ? 1u : e;
+  *ticket = 0u;
+}
+
 __global__ void k_partial_dot(const double* __restrict__ a, const double* __restrict__ b, long long n,
                               double* __restrict__ partial) {
   double acc = 0.0;
@@ -230,17 +246,19 @@ rfm_status rfm_launch_jmv(rfm_problem* p, const double* x, double* y) {
   rfm_prof_work(PF_JMV, 8.0 * ((double)(p->m + p->m_iface) * p->W + p->m + p->n));
   long long g = (p->m + 7) / 8;
   if (g > 152 * 64) g = 152 * 64;
-  k_jmv<<<(int)g, 256, 0, p->stream>>>(p->Jp, p->Js, p->rmeta, p->m, p->m_int, p->W, x, 1.0, 0.0, y);
+  k_jmv<<<(int)g, 256, 0, p->stream>>>(p->Jp, p->Js, p->rmeta, p->m, p->m_int, p->W, x, 1.0, 0.0, nullptr, p->skip,
+                                       y);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }
 
-rfm_status rfm_launch_jmv_axpby(rfm_problem* p, const double* x, double s1, double s2, double* y) {
+rfm_status rfm_launch_jmv_axpby(rfm_problem* p, const double* x, double s1, double s2, double* y,
+                                const double* s2dev) {
   ProfScope ps(PF_JMV, p->stream);
   rfm_prof_work(PF_JMV, 8.0 * ((double)(p->m + p->m_iface) * p->W + 2.0 * p->m + p->n));
   long long g = (p->m + 7) / 8;
   if (g > 152 * 64) g = 152 * 64;
-  k_jmv<<<(int)g, 256, 0, p->stream>>>(p->Jp, p->Js, p->rmeta, p->m, p->m_int, p->W, x, s1, s2, y);
+  k_jmv<<<(int)g, 256, 0, p->stream>>>(p->Jp, p->Js, p->rmeta, p->m, p->m_int, p->W, x, s1, s2, s2dev, p->skip, y);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }
@@ -249,7 +267,7 @@ rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y) {
   dim3 grid(p->G, (p->W + 63) / 64);
   ProfScope ps(PF_JTMV, p->stream);
   rfm_prof_work(PF_JTMV, 8.0 * ((double)(p->m + p->m_iface) * p->W + p->m + p->n));
-  k_jtmv<<<grid, 256, 0, p->stream>>>(p->Jp, p->Js, p->colptr, p->colrows, p->m_int, p->W, x, y);
+  k_jtmv<<<grid, 256, 0, p->stream>>>(p->Jp, p->Js, p->colptr, p->colrows, p->m_int, p->W, x, p->skip, y);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }
@@ -261,17 +279,16 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
     rfm_set_error("trsv: too many blocks");
     return RFM_EINVAL;
   }
-  p->epoch += 1;
-  if (p->epoch == 0) p->epoch = 1;
-  RFM_CUDA(cudaMemsetAsync(p->sync + SYNC_TICKET, 0, sizeof(unsigned int), p->stream));
+  k_trsv_prep<<<1, 1, 0, p->stream>>>(p->sync + SYNC_EPOCH, p->sync + SYNC_TICKET);
+  RFM_CHECK_LAUNCH();
   ProfScope ps(PF_TRSV, p->stream);
   rfm_prof_work(PF_TRSV, 8.0 * (double)n * (n + 1) / 2 + 16.0 * n);  // R read once, b and x
   if (trans == 0)
-    k_trsv<0><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->epoch,
-                                           p->sync + SYNC_TICKET, p->sync + SYNC_ERR);
+    k_trsv<0><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->sync + SYNC_EPOCH,
+                                           p->sync + SYNC_TICKET, p->sync + SYNC_ERR, p->skip);
   else
-    k_trsv<1><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->epoch,
-                                           p->sync + SYNC_TICKET, p->sync + SYNC_ERR);
+    k_trsv<1><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->sync + SYNC_EPOCH,
+                                           p->sync + SYNC_TICKET, p->sync + SYNC_ERR, p->skip);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }

@@ -445,4 +445,192 @@ rfm_status rfm_feature_gram(const rfm_problem* p, const double* pts_dev, int64_t
   return st;
 }
 
+
 }  // extern "C"
+
+// ---- warm-start object: basis of training solutions + network ------------
+
+namespace {
+
+// per input dimension: mean and standard deviation over the training set
+__global__ void k_input_stats(const double* __restrict__ P, int N, int din, float* __restrict__ mu,
+                              float* __restrict__ sd) {
+  const int i = threadIdx.x;
+  if (i >= din) return;
+  double s = 0.0, s2 = 0.0;
+  for (int j = 0; j < N; ++j) s += P[(size_t)j * din + i];
+  const double m = s / N;
+  for (int j = 0; j < N; ++j) {
+    const double d = P[(size_t)j * din + i] - m;
+    s2 += d * d;
+  }
+  const double v = s2 / N;
+  mu[i] = (float)m;
+  sd[i] = v > 0.0 ? (float)sqrt(v) : 1.0f;
+}
+
+__global__ void k_normalise_inputs(const double* __restrict__ P, long long count, int din, const float* __restrict__ mu,
+                                   const float* __restrict__ sd, float* __restrict__ x) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count * din;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % din);
+    x[t] = ((float)P[t] - mu[i]) / sd[i];
+  }
+}
+
+// t[j][k] = Z[j][k] / scale (FP32), k < rank, from Z [N][N]; also the sum of squares
+__global__ void k_targets(const double* __restrict__ Z, int N, int rank, double inv, float* __restrict__ t) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)N * rank;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long j = q / rank, k = q - j * rank;
+    t[q] = (float)(Z[(size_t)j * N + k] * inv);
+  }
+}
+
+__global__ void k_sumsq_rows(const double* __restrict__ Z, int N, int rank, double* __restrict__ out) {
+  // one thread per snapshot; fixed order
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double s = 0.0;
+  for (int k = 0; k < rank; ++k) s += Z[(size_t)j * N + k] * Z[(size_t)j * N + k];
+  out[j] = s;
+}
+
+}  // namespace
+
+struct rfm_warmstart {
+  rfm_mlp* net = nullptr;
+  cudaStream_t st = nullptr;
+  int din = 0, rank = 0, ntrain = 0;
+  long long n = 0;
+  double zscale = 1.0;
+  double *mean = nullptr, *U = nullptr;
+  float *mu = nullptr, *sd = nullptr, *x = nullptr, *t = nullptr, *xq = nullptr, *yq = nullptr;
+  int qcap = 0;
+};
+
+namespace {
+void ws_free(rfm_warmstart* w) {
+  if (!w) return;
+  if (w->net) rfm_mlp_destroy(w->net);
+  void* b[] = {w->mean, w->U, w->mu, w->sd, w->x, w->t, w->xq, w->yq};
+  for (void* q : b)
+    if (q) cudaFree(q);
+  delete w;
+}
+}  // namespace
+
+extern "C" {
+
+rfm_status rfm_warmstart_create(const rfm_problem* p, const double* C_dev, const double* params_dev, int N, int din,
+                                const double* pts_dev, int64_t npts, double tol, int hidden, uint64_t seed,
+                                rfm_warmstart** out) {
+  if (!p || !C_dev || !params_dev || N < 2 || din <= 0 || din > 1024 || !pts_dev || npts <= 0 || hidden <= 0 ||
+      !out) {
+    rfm_set_error("rfm_warmstart_create: bad argument");
+    return RFM_EINVAL;
+  }
+  rfm_warmstart* w = new rfm_warmstart();
+  w->st = p->stream;
+  w->din = din;
+  w->n = p->n;
+  w->ntrain = N;
+  double *Uall = nullptr, *Z = nullptr, *ss = nullptr;
+  rfm_status st = RFM_OK;
+  auto fail = [&](rfm_status s, const char* msg) {
+    if (msg) rfm_set_error(msg);
+    if (Uall) cudaFree(Uall);
+    if (Z) cudaFree(Z);
+    if (ss) cudaFree(ss);
+    ws_free(w);
+    return s;
+  };
+  if (cudaMalloc((void**)&w->mean, (size_t)w->n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&Uall, (size_t)N * w->n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&Z, (size_t)N * N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&ss, (size_t)N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&w->mu, din * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&w->sd, din * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&w->x, (size_t)N * din * sizeof(float)) != cudaSuccess)
+    return fail(RFM_ENOMEM, "rfm_warmstart_create: allocation failed");
+  int rank = 0;
+  st = rfm_function_basis(p, C_dev, N, pts_dev, npts, tol, w->mean, Uall, Z, &rank);
+  if (st != RFM_OK) return fail(st, nullptr);
+  if (rank < 1) return fail(RFM_EINVAL, "rfm_warmstart_create: the training solutions span no direction");
+  w->rank = rank;
+  // modes, compacted to [rank][n]
+  if (cudaMalloc((void**)&w->U, (size_t)rank * w->n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&w->t, (size_t)N * rank * sizeof(float)) != cudaSuccess)
+    return fail(RFM_ENOMEM, "rfm_warmstart_create: allocation failed");
+  if (cudaMemcpyAsync(w->U, Uall, (size_t)rank * w->n * sizeof(double), cudaMemcpyDeviceToDevice, w->st) != cudaSuccess)
+    return fail(RFM_ECUDA, "rfm_warmstart_create: copy failed");
+  // coordinate scale: root mean square of the coordinates
+  k_sumsq_rows<<<(N + 255) / 256, 256, 0, w->st>>>(Z, N, rank, ss);
+  std::vector<double> ssh(N);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(ssh.data(), ss, N * sizeof(double), cudaMemcpyDeviceToHost, w->st) != cudaSuccess ||
+      cudaStreamSynchronize(w->st) != cudaSuccess)
+    return fail(RFM_ECUDA, "rfm_warmstart_create: CUDA error");
+  double tot = 0.0;
+  for (double v : ssh) tot += v;
+  w->zscale = sqrt(tot / ((double)N * rank));
+  if (!(w->zscale > 0.0)) w->zscale = 1.0;
+  k_targets<<<blocks_for((long long)N * rank), 256, 0, w->st>>>(Z, N, rank, 1.0 / w->zscale, w->t);
+  k_input_stats<<<1, 1024, 0, w->st>>>(params_dev, N, din, w->mu, w->sd);
+  k_normalise_inputs<<<blocks_for((long long)N * din), 256, 0, w->st>>>(params_dev, N, din, w->mu, w->sd, w->x);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(w->st) != cudaSuccess)
+    return fail(RFM_ECUDA, "rfm_warmstart_create: CUDA error");
+  cudaFree(Uall);
+  cudaFree(Z);
+  cudaFree(ss);
+  Uall = Z = ss = nullptr;
+  st = rfm_mlp_create(din, hidden, rank, seed, (void*)w->st, &w->net);
+  if (st != RFM_OK) return fail(st, nullptr);
+  *out = w;
+  return RFM_OK;
+}
+
+rfm_status rfm_warmstart_destroy(rfm_warmstart* w) {
+  if (w) cudaStreamSynchronize(w->st);
+  ws_free(w);
+  return RFM_OK;
+}
+
+int rfm_warmstart_rank(const rfm_warmstart* w) { return w ? w->rank : 0; }
+
+rfm_mlp* rfm_warmstart_network(rfm_warmstart* w) { return w ? w->net : nullptr; }
+
+rfm_status rfm_warmstart_train(rfm_warmstart* w, int steps, float lr, double* loss_host) {
+  if (!w || steps < 0 || !(lr > 0.0f)) {
+    rfm_set_error("rfm_warmstart_train: bad argument");
+    return RFM_EINVAL;
+  }
+  return rfm_mlp_train(w->net, w->x, w->t, w->ntrain, nullptr, 0, steps, lr, loss_host);
+}
+
+rfm_status rfm_warmstart_predict(rfm_warmstart* w, const double* params_dev, int batch, double* c_dev) {
+  if (!w || !params_dev || batch <= 0 || !c_dev) {
+    rfm_set_error("rfm_warmstart_predict: bad argument");
+    return RFM_EINVAL;
+  }
+  if (batch > w->qcap) {
+    if (w->xq) cudaFree(w->xq);
+    if (w->yq) cudaFree(w->yq);
+    w->xq = w->yq = nullptr;
+    w->qcap = 0;
+    if (cudaMalloc((void**)&w->xq, (size_t)batch * w->din * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&w->yq, (size_t)batch * w->rank * sizeof(float)) != cudaSuccess) {
+      rfm_set_error("rfm_warmstart_predict: allocation failed");
+      return RFM_ENOMEM;
+    }
+    w->qcap = batch;
+  }
+  k_normalise_inputs<<<blocks_for((long long)batch * w->din), 256, 0, w->st>>>(params_dev, batch, w->din, w->mu, w->sd,
+                                                                              w->xq);
+  RFM_CHECK_LAUNCH();
+  RFM_TRY(rfm_mlp_forward(w->net, w->xq, batch, w->yq));
+  return rfm_basis_combine(w->mean, w->U, w->n, w->rank, w->yq, batch, w->zscale, c_dev, (void*)w->st);
+}
+
+}  // extern "C"
+

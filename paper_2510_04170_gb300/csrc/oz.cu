@@ -505,7 +505,6 @@ __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict_
   }
 }
 
-int g_oz_attr = 0;
 
 size_t oz_smem_bytes() { return (size_t)ASTAGES * ATILE + 2 * MAXD * BTILE + sizeof(OzBars) + 1024; }
 
@@ -560,10 +559,9 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
     rfm_set_error("oz_gemm: bad digit counts");
     return RFM_EINVAL;
   }
-  if (!g_oz_attr) {
-    RFM_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes()));
-    g_oz_attr = 1;
-  }
+  static const cudaError_t attr =  // once, thread-safe
+      cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+  RFM_CUDA(attr);
   OzArgs a;
   a.A = Ad; a.B = Bd; a.pA = pA; a.pB = pB; a.Lmax = Lmax;
   a.mtiles = (int)((M + BM - 1) / BM);
@@ -579,11 +577,10 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
         if (p + q + 2 <= Lmax) ++pairs;
     rfm_prof_work(PF_OZ_GEMM, 2.0 * pairs * (double)M * (double)N * (double)K);  // bf16 tensor flops
   }
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    RFM_CUDA(cudaGetDevice(&dev));
-    RFM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int nsm = rfm_num_sms();
+  if (nsm == 0) {
+    rfm_set_error("oz_gemm: cannot query the device");
+    return RFM_ECUDA;
   }
   const long long tiles = (long long)a.mtiles * a.ntiles;
   k_oz_gemm<<<(unsigned)std::min<long long>(tiles, nsm), NTHREADS, oz_smem_bytes(), st>>>(a);

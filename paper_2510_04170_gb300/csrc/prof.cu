@@ -50,6 +50,20 @@ void rfm_prof_work(int fam, double units) {
 }
 
 void rfm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void rfm_count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long rfm_launches_now() { return g_launches.load(std::memory_order_relaxed); }
+bool rfm_prof_active() { return g_on; }
+
+int rfm_num_sms() {
+  static const int n = [] {  // initialised once, thread-safe
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    return v;
+  }();
+  return n;
+}
 
 void* rfm_prof_begin(int fam, cudaStream_t st) {
   if (!g_on || !((g_mask >> fam) & 1u)) return nullptr;

@@ -369,7 +369,6 @@ struct QrScratch {
   double* dg;
 };
 
-int g_num_sms = 0;
 int g_panel_occ = 0;
 
 }  // namespace
@@ -396,11 +395,11 @@ QrScratch carve(double* scratch, long long n) {
 }
 
 rfm_status qr_init_device() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    RFM_CUDA(cudaGetDevice(&dev));
-    RFM_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    RFM_CUDA(cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  static const cudaError_t attr = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       200 * 1024);  // once, thread-safe
+  if (attr != cudaSuccess || rfm_num_sms() == 0) {
+    rfm_set_error("householder: device set-up failed");
+    return RFM_ECUDA;
   }
   return RFM_OK;
 }
@@ -409,17 +408,23 @@ rfm_status qr_init_device() {
 // panels; the FP64 compact-WY update of each panel is applied to the columns
 // up to cend (cend >= c1).
 rfm_status factor_range(double* A, long long s, long long lda, long long c0, long long c1, long long cend,
-                        cudaStream_t st, const QrScratch& q, unsigned int* sync) {
+                        cudaStream_t st, const QrScratch& q, unsigned int* sync, int panel_cap) {
   unsigned int* bar = sync + SYNC_BAR;
   unsigned int* err = sync + SYNC_ERR;
+  const int nsm = rfm_num_sms();
   for (long long j0 = c0; j0 < c1; j0 += NB) {
     const int nbw = (int)std::min<long long>(NB, c1 - j0);
     const long long rows = s - j0;
     // rows per CTA: at least 64, at most what fits in 200 KB of shared memory
     const long long maxchunk = (200LL * 1024) / (NB * (long long)sizeof(double));
-    long long P = std::min<long long>((rows + 63) / 64, (long long)g_num_sms);
+    const long long cap = panel_cap > 0 ? std::min(panel_cap, nsm) : nsm;
+    long long P = std::min<long long>((rows + 63) / 64, cap);
     if (P < 1) P = 1;
     long long chunk = (rows + P - 1) / P;
+    if (chunk > maxchunk && cap < nsm) {  // the cap would overflow shared memory: take the fewest CTAs that fit
+      P = std::min<long long>((rows + maxchunk - 1) / maxchunk, nsm);
+      chunk = (rows + P - 1) / P;
+    }
     if (chunk > maxchunk) {
       rfm_set_error("householder: sketch too tall for the panel kernel");
       return RFM_EINVAL;
@@ -438,7 +443,7 @@ rfm_status factor_range(double* A, long long s, long long lda, long long c0, lon
     const long long nt = cend - j1;
     if (nt <= 0) continue;
     const long long ctiles = (nt + 63) / 64;
-    long long nz = (2LL * g_num_sms + ctiles - 1) / ctiles;
+    long long nz = (2LL * nsm + ctiles - 1) / ctiles;
     nz = std::max<long long>(1, std::min<long long>(nz, std::min<long long>(64, (rows + 255) / 256)));
     const long long kchunk = (rows + nz - 1) / nz;
     nz = (rows + kchunk - 1) / kchunk;
@@ -485,7 +490,8 @@ rfm_status finish_r(double* A, long long n, long long lda, cudaStream_t st, cons
 }  // namespace
 
 rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda, cudaStream_t st,
-                                   double* scratch, long long scratch_len, unsigned int* sync, int* rank_flag_host) {
+                                   double* scratch, long long scratch_len, unsigned int* sync, int* rank_flag_host,
+                                   int panel_cap, long long ncols) {
   if (s < n || n <= 0) {
     rfm_set_error("householder: need s >= n > 0");
     return RFM_EINVAL;
@@ -497,7 +503,8 @@ rfm_status rfm_householder_inplace(double* A, long long s, long long n, long lon
   RFM_TRY(qr_init_device());
   const QrScratch q = carve(scratch, n);
   RFM_CUDA(cudaMemsetAsync(sync + SYNC_BAR, 0, 2 * sizeof(unsigned int), st));
-  RFM_TRY(factor_range(A, s, lda, 0, n, n, st, q, sync));
+  const long long c1 = ncols < 0 ? n : std::min<long long>(n, ((ncols + NB - 1) / NB) * NB);
+  RFM_TRY(factor_range(A, s, lda, 0, c1, n, st, q, sync, panel_cap));
   return finish_r(A, n, lda, st, q, sync, rank_flag_host);
 }
 
@@ -731,7 +738,7 @@ long long rfm_householder_emulated_bytes(long long s, long long n) {
 
 rfm_status rfm_householder_emulated(double* A, long long s, long long n, long long lda, cudaStream_t st,
                                     double* scratch, long long scratch_len, unsigned int* sync, void* emu,
-                                    long long emu_bytes, int* rank_flag_host) {
+                                    long long emu_bytes, int* rank_flag_host, int panel_cap, long long ncols) {
   if (s < n || n <= 0) {
     rfm_set_error("householder: need s >= n > 0");
     return RFM_EINVAL;
@@ -741,11 +748,11 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
     return RFM_EINVAL;
   }
   RFM_TRY(qr_init_device());
-  static bool t_attr = false;
-  if (!t_attr) {
-    RFM_CUDA(cudaFuncSetAttribute(k_block_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(QB * (QB + 1) * sizeof(double))));
-    t_attr = true;
+  static const cudaError_t t_attr = cudaFuncSetAttribute(k_block_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)(QB * (QB + 1) * sizeof(double)));
+  if (t_attr != cudaSuccess) {
+    rfm_set_error("householder: k_block_t shared-memory attribute");
+    return RFM_ECUDA;
   }
   const QrScratch q = carve(scratch, n);
   char* w = static_cast<char*>(emu);
@@ -769,12 +776,13 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
   int* e_w2 = reinterpret_cast<int*>(take(4LL * n));
   unsigned int* err = sync + SYNC_ERR;
   RFM_CUDA(cudaMemsetAsync(sync + SYNC_BAR, 0, 2 * sizeof(unsigned int), st));
-  for (long long J0 = 0; J0 < n; J0 += QB) {
+  const long long cstop = ncols < 0 ? n : std::min<long long>(n, ncols);
+  for (long long J0 = 0; J0 < cstop; J0 += QB) {
     const long long c1 = std::min<long long>(n, J0 + QB);
     const int nbw = (int)(c1 - J0);
     const long long rows = s - J0;
     const long long nt = n - c1;
-    RFM_TRY(factor_range(A, s, lda, J0, c1, c1, st, q, sync));
+    RFM_TRY(factor_range(A, s, lda, J0, c1, c1, st, q, sync, panel_cap));
     if (nt <= 0) break;
     {
       ProfScope ps(PF_QR_PANEL, st);

@@ -86,8 +86,18 @@ struct rfm_problem {
   long long work_cap = 0;
   double* red = nullptr;    // reduction partials
   unsigned int* sync = nullptr;  // counters / flags / error words
-  unsigned int epoch = 0;
   double* hostbuf = nullptr;     // pinned host scalars
+  // LSQR iterations run from device-resident scalars; while they run, the
+  // iteration's kernels return at once once *skip (the convergence flag) is set
+  const int* skip = nullptr;
+  void* lsqr_graph = nullptr;    // cudaGraphExec_t of one chunk of iterations
+  cudaStream_t cap_stream = nullptr;  // private stream the chunk is captured on
+  unsigned long long lsqr_graph_key = 0;
+  long long lsqr_graph_launches = 0;  // kernels per chunk (launch accounting)
+  int qr_panel_cap = 0;           // most CTAs per panel factorisation (0: one per SM)
+  // per-problem QR scratch (FP64 panel buffers)
+  double* qr_scratch = nullptr;
+  long long qr_scratch_len = 0;
 };
 
 // ---- error handling --------------------------------------------------------
@@ -101,6 +111,10 @@ void rfm_set_error(const std::string& msg);
     }                                                                           \
   } while (0)
 void rfm_count_launch();
+void rfm_count_launches(long long k);  // kernels run by one replay of a captured graph
+long long rfm_launches_now();
+bool rfm_prof_active();
+int rfm_num_sms();  // SMs of the current device (0 if it cannot be queried)
 #define RFM_CHECK_LAUNCH()                                                      \
   do {                                                                          \
     rfm_count_launch();                                                         \
@@ -153,7 +167,8 @@ rfm_status rfm_launch_gauss_sketch(rfm_problem* p, long long s, int kJ);
 rfm_status rfm_launch_gauss_sketch_tc(rfm_problem* p, long long s, int kJ);
 rfm_status rfm_householder_emulated(double* A, long long s, long long n, long long lda, cudaStream_t st,
                                     double* scratch, long long scratch_len, unsigned int* sync, void* emu,
-                                    long long emu_bytes, int* rank_flag_host);
+                                    long long emu_bytes, int* rank_flag_host, int panel_cap = 0,
+                                    long long ncols = -1);
 long long rfm_householder_emulated_bytes(long long s, long long n);
 rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* rows, long long K, long long m_int,
                                int W, int ndig, int* e, uint16_t* out, cudaStream_t st);
@@ -163,7 +178,10 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
 long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows);
 rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda,
                                    cudaStream_t st, double* scratch, long long scratch_len,
-                                   unsigned int* sync, int* rank_flag_host);
+                                   unsigned int* sync, int* rank_flag_host, int panel_cap = 0,
+                                   long long ncols = -1);
+// panel_cap: most CTAs of one panel factorisation (0: one per SM); ncols >= 0
+// stops after the blocks that cover the first ncols columns (timing probes).
 long long rfm_householder_scratch(long long s, long long n);
 // deterministic norms / dots: result written to out_dev[0]
 rfm_status rfm_norm2(cudaStream_t st, const double* x, long long n, double* partial, double* out_dev);
@@ -223,5 +241,7 @@ inline int rfm_swz128(int r, int k) {
 // layout of p->sync
 #define SYNC_ERR 0
 #define SYNC_TICKET 8
+#define SYNC_EPOCH 9
+#define SYNC_LSQR_DONE 10
 #define SYNC_BAR 16
 #define SYNC_FLAGS 64

@@ -20,7 +20,10 @@ EXPORTS = ["rfm_default_opts", "rfm_last_error", "rfm_problem_create", "rfm_prob
            "rfm_ipn_solve", "rfm_amipn_solve", "rfm_eval", "rfm_set_precision",
            "rfm_householder_r_tc", "rfm_emulated_dgemm", "rfm_mlp_create", "rfm_mlp_destroy",
            "rfm_mlp_num_params", "rfm_mlp_params", "rfm_mlp_forward", "rfm_mlp_gradient", "rfm_mlp_train",
-           "rfm_feature_gram", "rfm_function_basis", "rfm_basis_combine"]
+           "rfm_feature_gram", "rfm_function_basis", "rfm_basis_combine", "rfm_warmstart_create",
+           "rfm_warmstart_destroy", "rfm_warmstart_rank", "rfm_warmstart_network", "rfm_warmstart_train",
+           "rfm_warmstart_predict", "rfm_batch_create", "rfm_batch_destroy", "rfm_batch_size", "rfm_batch_problem",
+           "rfm_batch_solve", "rfm_autotune_qr"]
 
 
 class RfmError(RuntimeError):
@@ -102,6 +105,18 @@ def load(path=LIB_PATH):
         "rfm_feature_gram": (I, [P, VP, I64, ctypes.POINTER(I64), VP]),
         "rfm_function_basis": (I, [P, VP, I, VP, I64, D, VP, VP, VP, ctypes.POINTER(I)]),
         "rfm_basis_combine": (I, [VP, VP, I64, I, VP, I, D, VP, VP]),
+        "rfm_warmstart_create": (I, [P, VP, VP, I, I, VP, I64, D, I, ctypes.c_uint64, ctypes.POINTER(P)]),
+        "rfm_warmstart_destroy": (I, [P]),
+        "rfm_warmstart_rank": (I, [P]),
+        "rfm_warmstart_network": (P, [P]),
+        "rfm_warmstart_train": (I, [P, I, ctypes.c_float, ctypes.POINTER(D)]),
+        "rfm_warmstart_predict": (I, [P, VP, I, VP]),
+        "rfm_batch_create": (I, [VP, I, I, ctypes.POINTER(P)]),
+        "rfm_batch_destroy": (I, [P]),
+        "rfm_batch_size": (I, [P]),
+        "rfm_batch_problem": (P, [P, I]),
+        "rfm_batch_solve": (I, [P, VP, I, VP, VP, VP]),
+        "rfm_autotune_qr": (I, [I64, I64, VP, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -388,3 +403,94 @@ def rfm_basis_combine(mean, U, y, scale=1.0, stream=None):
     _check(load().rfm_basis_combine(_ptr(mean), _ptr(U), mean.shape[0], U.shape[0], _ptr(y.contiguous()), batch,
                                     scale, _ptr(c), _stream(stream)))
     return c
+
+
+class WarmStart:
+    """rfm_warmstart_*: basis of training solutions plus the coordinate network."""
+
+    def __init__(self, problem, C, params, pts, tol=1e-6, hidden=256, seed=1):
+        self._h = ctypes.c_void_p()
+        self.n = problem.n
+        _check(load().rfm_warmstart_create(problem._h, _ptr(C.contiguous()), _ptr(params.contiguous()), C.shape[0],
+                                           params.shape[1], _ptr(pts.contiguous()), pts.shape[0], tol, hidden, seed,
+                                           ctypes.byref(self._h)))
+        self.rank = load().rfm_warmstart_rank(self._h)
+
+    def close(self):
+        if self._h:
+            load().rfm_warmstart_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train(self, steps, lr=1e-3):
+        loss = ctypes.c_double()
+        _check(load().rfm_warmstart_train(self._h, steps, lr, ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, params):
+        c = torch.empty(params.shape[0], self.n, dtype=torch.float64, device="cuda")
+        _check(load().rfm_warmstart_predict(self._h, _ptr(params.contiguous()), params.shape[0], _ptr(c)))
+        return c
+
+
+class _BorrowedProblem(Problem):
+    """A problem owned by a batch (not destroyed by this handle)."""
+
+    def __init__(self, handle, desc):
+        lib = load()
+        self.desc = desc
+        self.stream = None
+        self._h = ctypes.c_void_p(handle)
+        v = [ctypes.c_int64() for _ in range(6)]
+        _check(lib.rfm_problem_sizes(self._h, *[ctypes.byref(x) for x in v]))
+        self.m, self.n, self.W, self.G, self.m_int, self.m_iface = (x.value for x in v)
+
+    def close(self):
+        self._h = ctypes.c_void_p()
+
+
+class Batch:
+    """rfm_batch_*: independent instances solved concurrently on one GPU."""
+
+    def __init__(self, descs, streams=4):
+        self.descs = list(descs)
+        arr = (ProblemDesc * len(self.descs))(*[make_desc(d) for d in self.descs])
+        self._h = ctypes.c_void_p()
+        _check(load().rfm_batch_create(arr, len(self.descs), streams, ctypes.byref(self._h)))
+        self.problems = [_BorrowedProblem(load().rfm_batch_problem(self._h, i), d) for i, d in enumerate(self.descs)]
+
+    def close(self):
+        if self._h:
+            load().rfm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, opts, solver="ipn", c0=None):
+        """Returns (list of solutions, list of info dicts, tuned precisions)."""
+        k = len(self.problems)
+        cs = [torch.zeros(p.n, dtype=torch.float64, device="cuda") if c0 is None else c0[i].clone()
+              for i, p in enumerate(self.problems)]
+        ptrs = (ctypes.c_void_p * k)(*[c.data_ptr() for c in cs])
+        infos = (SolveInfo * k)()
+        tuned = (ctypes.c_int * k)()
+        st = load().rfm_batch_solve(self._h, ctypes.byref(make_opts(opts)), 0 if solver == "ipn" else 1, ptrs, infos,
+                                    tuned)
+        _check(st, ok=(RFM_OK, RFM_ENOCONV))
+        return cs, [i.as_dict() for i in infos], list(tuned)
+
+
+def rfm_autotune_qr(s, n, stream=None):
+    prec, cap = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_double * 4)()
+    _check(load().rfm_autotune_qr(s, n, _stream(stream), ctypes.byref(prec), ctypes.byref(cap), ms))
+    return prec.value, cap.value, list(ms)

@@ -28,11 +28,6 @@ def sample_params(count, seed):
     return np.stack([kappa, amp, freq], axis=1)
 
 
-def normalise(params):
-    p = np.asarray(params, dtype=np.float64)
-    return np.stack([(p[:, 0] - 5.05) / 4.95, (p[:, 1] - 1.25) / 0.75, (p[:, 2] - 2.5) / 1.5], axis=1).astype(np.float32)
-
-
 def family_desc(params, base=None):
     kappa, amp, freq = (float(v) for v in params)
     d = base(kappa, amp, freq) if base else W.config_c5(kappa, amp, freq)
@@ -66,42 +61,21 @@ def solve(desc, opts, c0=None, solver="ipn"):
     return gp, c, info
 
 
-class WarmStart:
-    """Trained warm start: basis (mean, modes U, coordinate scale) plus the
-    network that maps normalised parameters to scaled coordinates."""
-
-    def __init__(self, net, mean, U, scale, losses):
-        self.net, self.mean, self.U, self.scale, self.losses = net, mean, U, scale, losses
-
-    @property
-    def rank(self):
-        return self.U.shape[0]
-
-    def predict(self, params):
-        y = self.net.forward(torch.as_tensor(normalise(params), device="cuda"))
-        return rfm.rfm_basis_combine(self.mean, self.U, y, self.scale)
-
-
 def train_warm_start(train_params, train_c, metric_desc, hidden=256, steps=3000, lr=1e-3, seed=1, tol=1e-6):
-    """Builds the function-space basis of the training solutions (on the
-    evaluation grid of `metric_desc`) and trains the network on their scaled
-    coordinates; the coordinates are orthonormal in u-space, so the plain mean
-    square of the coordinate error is the mean-square error of u_0."""
+    """Builds the warm start (rfm_warmstart_*) from training solutions and
+    trains it for `steps` full-batch Adam steps; returns it with the losses."""
     gp = rfm.Problem(metric_desc)
     X = torch.as_tensor(W.eval_grid(metric_desc), device="cuda")
     C = torch.as_tensor(np.asarray(train_c, dtype=np.float64), device="cuda")
-    mean, U, Z = rfm.rfm_function_basis(gp, C, X, tol=tol)
-    scale = float(torch.sqrt(torch.mean(Z * Z)))
-    net = rfm.MLP(3, hidden, U.shape[0], seed=seed)
-    x = torch.as_tensor(normalise(train_params), device="cuda")
-    t = (Z / scale).float().contiguous()
-    losses = []
+    P = torch.as_tensor(np.asarray(train_params, dtype=np.float64), device="cuda")
+    ws = rfm.WarmStart(gp, C, P, X, tol=tol, hidden=hidden, seed=seed)
+    ws.losses = []
     done = 0
     while done < steps:
         k = min(500, steps - done)
-        losses.append(net.train(x, t, k, lr))
+        ws.losses.append(ws.train(k, lr))
         done += k
-    return WarmStart(net, mean, U, scale, losses)
+    return ws
 
 
 def run(n_train=512, n_test=128, solver="ipn", precision=2, steps=3000, base=None, seed_train=1, seed_test=10001):
@@ -120,7 +94,7 @@ def run(n_train=512, n_test=128, solver="ipn", precision=2, steps=3000, base=Non
     t0 = time.perf_counter()
     ws = train_warm_start(ptrain, np.stack(targets), metric_desc, steps=steps)
     t_train = time.perf_counter() - t0
-    c0s = ws.predict(ptest).cpu().numpy()
+    c0s = ws.predict(torch.as_tensor(ptest, device="cuda")).cpu().numpy()
     rows = []
     for prm, c0 in zip(ptest, c0s):
         d = family_desc(prm, base)
