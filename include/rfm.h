@@ -252,13 +252,13 @@ rfm_status rfm_batch_solve(rfm_batch* b, const rfm_solve_opts* opts, int solver,
                            rfm_solve_info* infos, int* tuned_precision_out);
 /* QR autotuner: times the first 128 columns of a seeded random s x n
  * factorisation for the FP64 path (precision 0) and the tensor-core path
- * (precision 2), each with the panel spread over all SMs and over half of
- * them, and returns the fastest (cached per (s, n) for the process).
- * ms4_out (nullable) receives the four probe times in ms in the order
- * {FP64 all, FP64 half, TC all, TC half}.  Allocates a probe matrix of s*n
- * doubles plus the QR buffers. */
+ * (precision 2), each with the panel factorisation capped at 16, 32, 64 and
+ * all SMs' CTAs, and returns the fastest (cached per (s, n) for the process).
+ * ms8_out (nullable) receives the eight probe times in ms, FP64 caps first,
+ * then tensor-core caps, caps in the order above.  Allocates a probe matrix
+ * of s*n doubles plus the QR buffers. */
 rfm_status rfm_autotune_qr(int64_t s, int64_t n, void* cuda_stream, int* precision_out, int* panel_cap_out,
-                           double* ms4_out);
+                           double* ms8_out);
 
 /* ---- Learned warm start (an addition of this library; the paper starts
  * Newton from a fixed guess): an MLP maps PDE parameters to an initial

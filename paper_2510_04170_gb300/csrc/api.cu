@@ -551,8 +551,8 @@ rfm_status lsqr(rfm_problem* p, const double* b, double eta, double conlim, long
   k_lsqr_init<<<1, 1, 0, st>>>(lst, sc, eta, conlim, (double)iter_lim, done);
   RFM_CHECK_LAUNCH();
   // chunks of iterations until the device sets done; replayed from a graph
-  // unless per-kernel profiling is on (event timing needs eager launches)
-  const bool graph = !rfm_prof_active();
+  // unless LSQR's own kernels are being timed (event timing needs eager launches)
+  const bool graph = !rfm_prof_active((1u << PF_TRSV) | (1u << PF_JMV) | (1u << PF_JTMV) | (1u << PF_VECTOR));
   p->skip = done;
   rfm_status r = RFM_OK;
   if (graph) r = lsqr_graph(p, lst, done);

@@ -14,7 +14,9 @@
 //
 // The autotuner picks, per sketch size (s, n), the QR configuration: FP64
 // panels with the FP64 trailing update, or the tensor-core (emulated FP64)
-// trailing update, each with the panel spread over all SMs or half of them.
+// trailing update, each with the panel factorisation spread over at most 16,
+// 32, 64 or all SMs (fewer CTAs make the two grid barriers per column cheaper,
+// more CTAs share the panel's rows; shared memory bounds the rows per CTA).
 // Each candidate factors the first 128 columns of a seeded random s x n
 // matrix (updating all n columns), timed with CUDA events after one warm-up;
 // the fastest is cached per (s, n) for the process.
@@ -44,10 +46,13 @@ __global__ void k_fill_probe(double* __restrict__ A, long long count, unsigned l
   }
 }
 
+constexpr int kCaps = 4;              // panel CTA caps tried: 16, 32, 64, all SMs
+constexpr int kCands = 2 * kCaps;     // x {FP64 update, tensor-core update}
+
 struct QrChoice {
   int precision = 0;
   int panel_cap = 0;
-  double ms[4] = {0, 0, 0, 0};
+  double ms[kCands] = {};
 };
 
 std::mutex g_tune_mu;
@@ -74,10 +79,10 @@ rfm_status probe_qr(long long s, long long n, cudaStream_t st, QrChoice* out) {
     r = RFM_ENOMEM;
   }
   if (r == RFM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) r = RFM_ECUDA;
-  const int caps[2] = {nsm, std::max(1, nsm / 2)};
+  const int caps[kCaps] = {std::min(16, nsm), std::min(32, nsm), std::min(64, nsm), nsm};
   const long long ncols = std::min<long long>(n, 128);
-  for (int c = 0; c < 4 && r == RFM_OK; ++c) {
-    const int prec = c < 2 ? 0 : 2, cap = caps[c & 1];
+  for (int c = 0; c < kCands && r == RFM_OK; ++c) {
+    const int prec = c < kCaps ? 0 : 2, cap = caps[c % kCaps];
     float best = 1e30f;
     for (int rep = 0; rep < 2 && r == RFM_OK; ++rep) {  // first run warms up
       k_fill_probe<<<(unsigned)std::min<long long>((s * n + 255) / 256, 152 * 16), 256, 0, st>>>(A, s * n, 12345ull);
@@ -103,10 +108,10 @@ rfm_status probe_qr(long long s, long long n, cudaStream_t st, QrChoice* out) {
   }
   if (r == RFM_OK) {
     int arg = 0;
-    for (int c = 1; c < 4; ++c)
+    for (int c = 1; c < kCands; ++c)
       if (out->ms[c] < out->ms[arg]) arg = c;
-    out->precision = arg < 2 ? 0 : 2;
-    out->panel_cap = caps[arg & 1];
+    out->precision = arg < kCaps ? 0 : 2;
+    out->panel_cap = caps[arg % kCaps];
   }
   cudaStreamSynchronize(st);
   if (e0) cudaEventDestroy(e0);
@@ -167,7 +172,7 @@ struct rfm_batch {
 extern "C" {
 
 rfm_status rfm_autotune_qr(int64_t s, int64_t n, void* cuda_stream, int* precision_out, int* panel_cap_out,
-                           double* ms4_out) {
+                           double* ms8_out) {
   if (s < n || n <= 0) {
     rfm_set_error("rfm_autotune_qr: need s >= n > 0");
     return RFM_EINVAL;
@@ -176,8 +181,8 @@ rfm_status rfm_autotune_qr(int64_t s, int64_t n, void* cuda_stream, int* precisi
   RFM_TRY(tuned_qr(s, n, (cudaStream_t)cuda_stream, &c));
   if (precision_out) *precision_out = c.precision;
   if (panel_cap_out) *panel_cap_out = c.panel_cap;
-  if (ms4_out)
-    for (int i = 0; i < 4; ++i) ms4_out[i] = c.ms[i];
+  if (ms8_out)
+    for (int i = 0; i < kCands; ++i) ms8_out[i] = c.ms[i];
   return RFM_OK;
 }
 

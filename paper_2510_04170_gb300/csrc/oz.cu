@@ -138,6 +138,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// t 2^k: for a normal t whose scaled exponent stays normal, an integer add to
+// the exponent field (no FP64 instruction); otherwise (zero, subnormal or out
+// of range) ldexp.
+__device__ __forceinline__ double scale_pow2(double t, int k) {
+  const long long b = __double_as_longlong(t);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E != 0 && E + k > 0 && E + k < 2047) return __longlong_as_double(b + ((long long)k << 52));
+  return ldexp(t, k);
+}
+
 // ---------------------------------------------------------------- GEMM kernel
 struct OzArgs {
   const uint16_t* A;  // digit tiles [pA][mtiles][ktiles][ATILE/2]
@@ -355,8 +365,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
           const long long gj = (long long)nt * BN + col0 + j;
           if (gj < g.N) {
             // value = 2^(e+f) [ I 2^(-4 BETA) + tail 2^(-5 BETA) ], I in units of level 3
-            const double tot = (double)ai[j] + at[j] * (1.0 / (double)(1 << BETA));
-            const double val = ldexp(tot, ei + g.eb[gj] - 5 * BETA);
+            const double tot = fma(at[j], 1.0 / (double)(1 << BETA), (double)ai[j]);
+            const double val = scale_pow2(tot, ei + g.eb[gj] - 5 * BETA);
             double* cp = g.C + gi + gj * g.ldc;
             if (g.mode == 0) *cp = val;
             else *cp -= val;
@@ -443,8 +453,12 @@ __global__ void k_rowexp(Acc X, long long R, long long K, int* __restrict__ e) {
 }
 
 // Balanced base-2^7 digits of x 2^-e (|x| < 2^e): V = round(x 2^(7 ndig - e))
-// as an integer built from the mantissa bits, then d_ndig .. d_2 in
-// [-64, 63] peeled from the low end and d_1 = the rest (|d_1| <= 128).
+// as an integer built from the mantissa bits; the ndig-1 low digits lie in
+// [-64, 63] and d_1 takes the rest (|d_1| <= 128).  Adding the bias
+// 64 (1 + 2^7 + ... + 2^(7(ndig-2))) to V turns every low digit into the
+// plain 7-bit field (digit + 64) of U = V + bias, so each digit is one field
+// extract, and the top digit is U >> 7(ndig-1) (the same digits as peeling
+// V from its low end with nearest remainders).
 __device__ __forceinline__ void digits_of(double x, int e, int ndig, float* d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
@@ -456,13 +470,20 @@ __device__ __forceinline__ void digits_of(double x, int e, int ndig, float* d) {
   else if (sh > -63) V = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
   else V = 0;
   if (b >> 63) V = -V;
-  for (int p = ndig - 1; p >= 1; --p) {
-    long long r = V & 127;
-    if (r >= 64) r -= 128;
-    d[p] = (float)r;
-    V = (V - r) >> 7;
+  // bias = 64 (128^(ndig-1) - 1) / 127: ndig-1 seven-bit fields of value 64
+  const long long bias = (long long)(0x0001020408102040ull >> (7 * (MAXD - ndig)));
+  const long long U = V + bias;
+  const unsigned lo = (unsigned)U, hi = (unsigned)((unsigned long long)U >> 32);
+#pragma unroll
+  for (int dd = 1; dd < MAXD; ++dd) {  // plane dd holds bits 7 (ndig-1-dd) .. +6 of U (registers, not stack)
+    if (dd < ndig) {
+      const int bit = 7 * (ndig - 1 - dd);
+      const unsigned f = (bit < 32 ? __funnelshift_r(lo, hi, bit) : hi >> (bit - 32)) & 127u;
+      // exact float of f - 64: 2^23 + f minus (2^23 + 64)
+      d[dd] = __int_as_float((int)(0x4B000000u | f)) - 8388672.0f;
+    }
   }
-  d[0] = (float)V;
+  d[0] = (float)(int)(U >> (7 * (ndig - 1)));
 }
 
 // Digit tiles: out[d][rtile][ktile][tile], tile = TR rows x 64 k in the 128B

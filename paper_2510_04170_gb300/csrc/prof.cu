@@ -52,7 +52,7 @@ void rfm_prof_work(int fam, double units) {
 void rfm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void rfm_count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long rfm_launches_now() { return g_launches.load(std::memory_order_relaxed); }
-bool rfm_prof_active() { return g_on; }
+bool rfm_prof_active(unsigned int families) { return g_on && (g_mask & families) != 0; }
 
 int rfm_num_sms() {
   static const int n = [] {  // initialised once, thread-safe

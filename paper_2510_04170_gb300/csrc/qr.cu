@@ -105,11 +105,24 @@ __global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
       a.part[c * (NB + 2) + 1] = own ? v[j - rbeg] : 0.0;
     }
     grid_barrier(a.bar, a.P, a.err);
-    double sigma = 0.0, alpha = 0.0;
-    for (int q = 0; q < a.P; ++q) {
-      sigma += __ldcg(a.part + q * (NB + 2));
-      alpha += __ldcg(a.part + q * (NB + 2) + 1);
+    // sigma and alpha over all CTAs: warp 0 loads the partials lane-strided
+    // (all loads in flight at once) and sums them in a fixed order, so every
+    // CTA obtains bitwise the same values
+    if (w == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int q = lane; q < a.P; q += 32) {
+        s0 += __ldcg(a.part + q * (NB + 2));
+        s1 += __ldcg(a.part + q * (NB + 2) + 1);
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      if (lane == 0) {
+        sh[33] = s0;
+        sh[34] = s1;
+      }
     }
+    __syncthreads();
+    const double sigma = sh[33], alpha = sh[34];
     double tau = 0.0, beta = alpha, scale = 0.0;
     if (sigma != 0.0) {
       const double nrm = sqrt(alpha * alpha + sigma);
@@ -135,10 +148,12 @@ __global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
       if (lane == 0) a.part[c * (NB + 2) + 2 + kk] = acc;
     }
     grid_barrier(a.bar, a.P, a.err);
-    for (int kk = tid; kk < rest; kk += blockDim.x) {
+    // w_k over all CTAs: one warp per k, partials loaded lane-strided
+    for (int kk = w; kk < rest; kk += (blockDim.x >> 5)) {
       double s = 0.0;
-      for (int q = 0; q < a.P; ++q) s += __ldcg(a.part + q * (NB + 2) + 2 + kk);
-      sw[kk] = s;
+      for (int q = lane; q < a.P; q += 32) s += __ldcg(a.part + q * (NB + 2) + 2 + kk);
+      s = warp_sum(s);
+      if (lane == 0) sw[kk] = s;
     }
     __syncthreads();
     if (tau != 0.0) {
@@ -180,24 +195,33 @@ __global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
     __shared__ double G[NB][NB + 1];
     __shared__ double Ts[NB][NB + 1];
     for (int pq = tid; pq < a.nbw * a.nbw; pq += blockDim.x) {
+      // sum over CTAs in increasing order, eight loads in flight
       double s = 0.0;
-      for (int q = 0; q < a.P; ++q) s += __ldcg(a.gram + (size_t)q * NB * NB + pq);
+      int q = 0;
+      for (; q + 8 <= a.P; q += 8) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = __ldcg(a.gram + (size_t)(q + u) * NB * NB + pq);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += t[u];
+      }
+      for (; q < a.P; ++q) s += __ldcg(a.gram + (size_t)q * NB * NB + pq);
       G[pq / a.nbw][pq % a.nbw] = s;
     }
+    for (int pq = tid; pq < NB * (NB + 1); pq += blockDim.x) Ts[pq / (NB + 1)][pq % (NB + 1)] = 0.0;
     __syncthreads();
-    if (tid == 0) {
-      for (int jj = 0; jj < a.nbw; ++jj) {
-        const double tj = __ldcg(a.tau + a.j0 + jj);
-        for (int i = 0; i < jj; ++i) {
-          double s = 0.0;
-          for (int l = i; l < jj; ++l) s += Ts[i][l] * G[l][jj];
-          Ts[i][jj] = -tj * s;
-        }
+    // T column by column (compact WY: T[:j, j] = -tau_j T[:j, :j] G[:j, j]); rows in parallel
+    for (int jj = 0; jj < a.nbw; ++jj) {
+      const double tj = __ldcg(a.tau + a.j0 + jj);
+      if (tid < jj) {
+        double s = 0.0;
+        for (int l = tid; l < jj; ++l) s += Ts[tid][l] * G[l][jj];
+        Ts[tid][jj] = -tj * s;
+      } else if (tid == jj) {
         Ts[jj][jj] = tj;
-        for (int i = jj + 1; i < a.nbw; ++i) Ts[i][jj] = 0.0;
       }
+      __syncthreads();
     }
-    __syncthreads();
     for (int pq = tid; pq < NB * NB; pq += blockDim.x) {
       const int p = pq / NB, q = pq % NB;
       a.T[pq] = (p < a.nbw && q < a.nbw) ? Ts[p][q] : 0.0;

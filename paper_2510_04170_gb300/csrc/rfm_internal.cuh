@@ -113,7 +113,7 @@ void rfm_set_error(const std::string& msg);
 void rfm_count_launch();
 void rfm_count_launches(long long k);  // kernels run by one replay of a captured graph
 long long rfm_launches_now();
-bool rfm_prof_active();
+bool rfm_prof_active(unsigned int families);  // are any of these families (bit masks) being timed?
 int rfm_num_sms();  // SMs of the current device (0 if it cannot be queried)
 #define RFM_CHECK_LAUNCH()                                                      \
   do {                                                                          \

@@ -491,6 +491,6 @@ class Batch:
 
 def rfm_autotune_qr(s, n, stream=None):
     prec, cap = ctypes.c_int(), ctypes.c_int()
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 8)()
     _check(load().rfm_autotune_qr(s, n, _stream(stream), ctypes.byref(prec), ctypes.byref(cap), ms))
     return prec.value, cap.value, list(ms)

@@ -51,24 +51,14 @@ def grouped_eval_points(desc, per_axis=10):
     return X[order], starts
 
 
-def solve(desc, opts, c0=None, solver="ipn"):
-    gp = rfm.Problem(desc)
-    c0t = None if c0 is None else torch.as_tensor(np.asarray(c0, dtype=np.float64), device="cuda")
-    t0 = time.perf_counter()
-    c, info = getattr(gp, f"rfm_{solver}_solve")(opts, c0t)
-    torch.cuda.synchronize()
-    info["wall_s"] = time.perf_counter() - t0
-    return gp, c, info
-
-
 def train_warm_start(train_params, train_c, metric_desc, hidden=256, steps=3000, lr=1e-3, seed=1, tol=1e-6):
-    """Builds the warm start (rfm_warmstart_*) from training solutions and
-    trains it for `steps` full-batch Adam steps; returns it with the losses."""
+    """Builds the warm start (rfm_warmstart_*) from training solutions (CUDA
+    tensor [N][n]) and trains it for `steps` full-batch Adam steps; returns it
+    with the losses."""
     gp = rfm.Problem(metric_desc)
     X = torch.as_tensor(W.eval_grid(metric_desc), device="cuda")
-    C = torch.as_tensor(np.asarray(train_c, dtype=np.float64), device="cuda")
     P = torch.as_tensor(np.asarray(train_params, dtype=np.float64), device="cuda")
-    ws = rfm.WarmStart(gp, C, P, X, tol=tol, hidden=hidden, seed=seed)
+    ws = rfm.WarmStart(gp, train_c.contiguous(), P, X, tol=tol, hidden=hidden, seed=seed)
     ws.losses = []
     done = 0
     while done < steps:
@@ -78,37 +68,46 @@ def train_warm_start(train_params, train_c, metric_desc, hidden=256, steps=3000,
     return ws
 
 
-def run(n_train=512, n_test=128, solver="ipn", precision=2, steps=3000, base=None, seed_train=1, seed_test=10001):
-    """Full experiment: solve n_train instances for targets, train, then solve
-    n_test held-out instances from c_0 = 0 and from the network's c_0."""
+def _timed(fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def run(n_train=512, n_test=128, solver="ipn", precision=2, steps=3000, base=None, streams=4, seed_train=1,
+        seed_test=10001):
+    """Full experiment: batch-solve n_train instances for the targets, train,
+    then batch-solve the n_test held-out instances from c_0 = 0 and from the
+    network's c_0 and compare Jacobian counts, times and solutions."""
     opts = W.solve_opts(precision=precision)
     ptrain = sample_params(n_train, seed_train)
     ptest = sample_params(n_test, seed_test)
-    targets = []
-    t0 = time.perf_counter()
-    for prm in ptrain:
-        _, c, info = solve(family_desc(prm, base), opts, solver=solver)
-        targets.append(c.cpu().numpy())
-    t_data = time.perf_counter() - t0
-    metric_desc = family_desc(ptrain[0], base)
-    t0 = time.perf_counter()
-    ws = train_warm_start(ptrain, np.stack(targets), metric_desc, steps=steps)
-    t_train = time.perf_counter() - t0
-    c0s = ws.predict(torch.as_tensor(ptest, device="cuda")).cpu().numpy()
+    bt = rfm.Batch([family_desc(p, base) for p in ptrain], streams=streams)
+    (ctrain, _, _), t_data = _timed(lambda: bt.solve(opts, solver=solver))
+    bt.close()
+    ws, t_train = _timed(lambda: train_warm_start(ptrain, torch.stack(ctrain), family_desc(ptrain[0], base),
+                                                  steps=steps))
+    c0, t_pred = _timed(lambda: ws.predict(torch.as_tensor(ptest, device="cuda")))
+    be = rfm.Batch([family_desc(p, base) for p in ptest], streams=streams)
+    (cz, iz, _), t_zero = _timed(lambda: be.solve(opts, solver=solver))
+    (cw, iw, _), t_warm = _timed(lambda: be.solve(opts, solver=solver, c0=[c0[i] for i in range(n_test)]))
     rows = []
-    for prm, c0 in zip(ptest, c0s):
-        d = family_desc(prm, base)
-        gz, cz, iz = solve(d, opts, solver=solver)
-        gw, cw, iw = solve(d, opts, c0=c0, solver=solver)
-        Xe = torch.as_tensor(W.eval_grid(d), device="cuda")
-        uz = gz.rfm_eval(cz, Xe).cpu().numpy()
-        uw = gw.rfm_eval(cw, Xe).cpu().numpy()
-        u0 = gw.rfm_eval(torch.as_tensor(c0, device="cuda"), Xe).cpu().numpy()
-        rows.append(dict(it_zero=iz["outer_iters"], it_warm=iw["outer_iters"], nj_zero=iz["n_jac"], nj_warm=iw["n_jac"],
-                         t_zero=iz["t_total"], t_warm=iw["t_total"], res_zero=iz["final_resid"],
-                         res_warm=iw["final_resid"],
+    for i, prm in enumerate(ptest):
+        Xe = torch.as_tensor(W.eval_grid(family_desc(prm, base)), device="cuda")
+        gp = be.problems[i]
+        uz = gp.rfm_eval(cz[i], Xe).cpu().numpy()
+        uw = gp.rfm_eval(cw[i], Xe).cpu().numpy()
+        u0 = gp.rfm_eval(c0[i].contiguous(), Xe).cpu().numpy()
+        rows.append(dict(it_zero=iz[i]["outer_iters"], it_warm=iw[i]["outer_iters"], nj_zero=iz[i]["n_jac"],
+                         nj_warm=iw[i]["n_jac"], lsqr_zero=iz[i]["lsqr_iters_total"],
+                         lsqr_warm=iw[i]["lsqr_iters_total"], res_zero=iz[i]["final_resid"],
+                         res_warm=iw[i]["final_resid"],
                          rel_warm_vs_zero=float(np.linalg.norm(uw - uz) / np.linalg.norm(uz)),
                          rel_guess=float(np.linalg.norm(u0 - uz) / np.linalg.norm(uz))))
     agg = {k: float(np.mean([r[k] for r in rows])) for k in rows[0]}
-    return dict(n_train=n_train, n_test=n_test, solver=solver, t_data_s=t_data, t_train_s=t_train, rank=ws.rank,
+    return dict(n_train=n_train, n_test=n_test, solver=solver, precision=precision, streams=streams,
+                t_data_s=t_data, t_train_s=t_train, t_predict_s=t_pred, t_zero_s=t_zero, t_warm_s=t_warm,
+                solves_per_s_zero=n_test / t_zero, solves_per_s_warm=n_test / (t_warm + t_pred), rank=ws.rank,
                 final_loss=ws.losses[-1], mean=agg, rows=rows)
