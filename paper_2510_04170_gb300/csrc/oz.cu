@@ -13,11 +13,14 @@
 // and every L_l of the leading levels accumulated over a K-chunk of 512 is an
 // integer below 2^24, so its FP32 tensor-core accumulation is exact.  Per
 // chunk the four leading levels combine exactly into the int64
-// L_0 2^21 + L_1 2^14 + L_2 2^7 + L_3 (summed over chunks in int64), the
-// remaining levels by an FP32 Horner sum (rounding ~2^-52 of the leading
-// term) summed over chunks in FP64; both are merged once at the end and
-// over chunks in FP64; pairs with p + q > Lmax are dropped (their weight is
-// below 2^(-beta (Lmax+1)) relative to max|A_i.| max|B_.j|).
+// L_0 2^21 + L_1 2^14 + L_2 2^7 + L_3 and the four trailing ones into
+// L_4 2^21 + L_5 2^14 + L_6 2^7 + L_7 (their accumulators may pass 2^24 and
+// round there, ~2^-49 of the leading term's unit at level 7), both summed over
+// chunks in int64; at the end the 128-bit fixed-point value is rounded once
+// to FP64 with integer operations, so the epilogue issues one FP64
+// instruction per element (the C update).  Pairs with p + q > Lmax are
+// dropped (their weight is below 2^(-beta (Lmax+1)) relative to
+// max|A_i.| max|B_.j|).
 //
 // Kernel layout: persistent, one CTA per SM looping over 128 x 64 output
 // tiles, 10 warps.
@@ -49,6 +52,7 @@ constexpr int MAXD = 8;             // digits per operand
 constexpr int ASTAGES = 6;
 constexpr int EPI_WARPS = 8;        // two warps per TMEM lane quarter, 32 columns each
 constexpr int EPI_COLS = BN / (EPI_WARPS / 4);
+constexpr int EPI_GRP = 4;          // C elements loaded per round trip in the final update
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int KCHUNK = 8;           // k-tiles per exact chunk (8 * 64 = 512)
 constexpr int BETA = 7;
@@ -138,14 +142,48 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// t 2^k: for a normal t whose scaled exponent stays normal, an integer add to
-// the exponent field (no FP64 instruction); otherwise (zero, subnormal or out
-// of range) ldexp.
-__device__ __forceinline__ double scale_pow2(double t, int k) {
-  const long long b = __double_as_longlong(t);
-  const int E = (int)((b >> 52) & 0x7FF);
-  if (E != 0 && E + k > 0 && E + k < 2047) return __longlong_as_double(b + ((long long)k << 52));
-  return ldexp(t, k);
+// (ah 2^28 + al) 2^k rounded to the nearest double (ties to even) with integer
+// operations only: the 128-bit two's-complement sum, its leading bit, a 53-bit
+// mantissa with round and sticky bits, and the exponent field; ldexp of the
+// rounded mantissa where the result leaves the normal range.  |ah| < 2^63
+// keeps the leading bit below 2^91, so every shift below stays under 64.
+__device__ __forceinline__ double fix_to_double(long long ah, long long al, int k) {
+  long long h = ah >> 36;
+  const unsigned long long l0 = (unsigned long long)ah << 28;
+  const unsigned long long l = l0 + (unsigned long long)al;
+  h += (al >> 63) + (l < l0 ? 1 : 0);
+  const bool neg = h < 0;
+  unsigned long long H = (unsigned long long)h, L = l;
+  if (neg) {
+    L = ~L + 1ull;
+    H = ~H + (L == 0 ? 1ull : 0ull);
+  }
+  if ((H | L) == 0) return 0.0;
+  int msb = H ? 127 - __clzll((long long)H) : 63 - __clzll((long long)L);
+  const int sh = msb - 52;
+  unsigned long long mant;
+  bool up = false;
+  if (sh <= 0) {
+    mant = L << (-sh);
+  } else {
+    mant = (L >> sh) | (H << (64 - sh));
+    const unsigned long long rbit = (L >> (sh - 1)) & 1ull;
+    const bool sticky = (L & ((1ull << (sh - 1)) - 1ull)) != 0;
+    up = rbit && (sticky || (mant & 1ull));
+  }
+  if (up) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++msb;
+    }
+  }
+  const int e = msb + k + 1023;
+  if (e > 0 && e < 2047)
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)e << 52) |
+                                            (mant & ((1ull << 52) - 1ull))));
+  const double mv = (double)mant;  // exact: mant < 2^53
+  return ldexp(neg ? -mv : mv, msb - 52 + k);
 }
 
 // ---------------------------------------------------------------- GEMM kernel
@@ -297,17 +335,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     const int col0 = ((warp - 2) >> 2) * EPI_COLS;
     const int row = quarter * 32 + lane;
     const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
-    const float s32 = 1.0f / (float)(1 << BETA);
     unsigned cglob = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
       const int mt = t % g.mtiles, nt = t / g.mtiles;
-      long long ai[EPI_COLS];
-      double at[EPI_COLS];  // tail levels, one FP64 add per element per chunk
+      long long ai[EPI_COLS];  // levels 0-3, in units of level 3
+      long long al[EPI_COLS];  // levels 4-7, in units of level 7
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) {
         ai[j] = 0;
-        at[j] = 0.0;
+        al[j] = 0;
       }
       for (int c = 0; c < nchunks; ++c) {
         const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, cglob & 1, g.err, 9));
@@ -338,17 +375,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) ai[grp * 8 + i] += I[i];
-          // remaining levels: FP32 Horner, summed over chunks in FP64
+          // remaining levels, combined the same way in int64 (their FP32
+          // accumulators may exceed 2^24 and round there, far below the
+          // result's last bit; the values stay integers below 2^31)
           if (nlev > 4) {
-            float tl[8];
-            tmem_ld8(cbase + (uint32_t)((nlev - 1) * BN), tl);
-            for (int l = nlev - 2; l >= 4; --l) {
-              tmem_ld8(cbase + (uint32_t)(l * BN), v);
+            tmem_ld8(cbase + (uint32_t)(4 * BN), v);
 #pragma unroll
-              for (int i = 0; i < 8; ++i) tl[i] = fmaf(tl[i], s32, v[i]);
+            for (int i = 0; i < 8; ++i) I[i] = (long long)__float2int_rn(v[i]);
+            for (int l = 5; l < 8; ++l) {
+              if (l < nlev) {
+                tmem_ld8(cbase + (uint32_t)(l * BN), v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) I[i] = (I[i] << BETA) + (long long)__float2int_rn(v[i]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) I[i] <<= BETA;
+              }
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) at[grp * 8 + i] += (double)tl[i];
+            for (int i = 0; i < 8; ++i) al[grp * 8 + i] += I[i];
           }
         }
         tc_fence_before();
@@ -360,16 +405,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
       const long long gi = (long long)mt * BM + row;
       if (gi < g.M) {
         const int ei = g.ea[gi];
+        // EPI_GRP columns at a time: their exponents and (mode 1) C values are
+        // loaded together, so one memory round trip serves EPI_GRP elements
 #pragma unroll
-        for (int j = 0; j < EPI_COLS; ++j) {
-          const long long gj = (long long)nt * BN + col0 + j;
-          if (gj < g.N) {
-            // value = 2^(e+f) [ I 2^(-4 BETA) + tail 2^(-5 BETA) ], I in units of level 3
-            const double tot = fma(at[j], 1.0 / (double)(1 << BETA), (double)ai[j]);
-            const double val = scale_pow2(tot, ei + g.eb[gj] - 5 * BETA);
-            double* cp = g.C + gi + gj * g.ldc;
-            if (g.mode == 0) *cp = val;
-            else *cp -= val;
+        for (int j0 = 0; j0 < EPI_COLS; j0 += EPI_GRP) {
+          double cv[EPI_GRP];
+          int eb[EPI_GRP];
+#pragma unroll
+          for (int i = 0; i < EPI_GRP; ++i) {
+            const long long gj = (long long)nt * BN + col0 + j0 + i;
+            const bool in = gj < g.N;
+            eb[i] = in ? __ldg(g.eb + gj) : 0;
+            cv[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < EPI_GRP; ++i) {
+            const long long gj = (long long)nt * BN + col0 + j0 + i;
+            if (gj < g.N) {
+              // value = 2^(e+f-9 BETA) (ai 2^(4 BETA) + al), one rounding to FP64
+              const double val = fix_to_double(ai[j0 + i], al[j0 + i], ei + eb[i] - 9 * BETA);
+              g.C[gi + gj * g.ldc] = g.mode == 0 ? val : cv[i] - val;
+            }
           }
         }
       }
