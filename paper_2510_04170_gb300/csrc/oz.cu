@@ -142,6 +142,28 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Levels l0 .. l0+3 of 8 columns (levels >= nlev read as 0) combined exactly,
+// L_l0 2^(3 BETA) + L_(l0+1) 2^(2 BETA) + L_(l0+2) 2^BETA + L_(l0+3), and
+// added to acc[0..7].  (Ten warps leave 168 registers a thread, which the
+// accumulators mostly fill, so one level is loaded per wait.)
+__device__ __forceinline__ void tmem_levels4(uint32_t cbase, int l0, int nlev, long long* acc) {
+  float v[8];
+  long long I[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (l0 + q < nlev) {  // warp-uniform
+      tmem_ld8(cbase + (uint32_t)((l0 + q) * BN), v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) I[i] = (q == 0 ? 0 : I[i] << BETA) + (long long)__float2int_rn(v[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) I[i] = q == 0 ? 0 : I[i] << BETA;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] += I[i];
+}
+
 // (ah 2^28 + al) 2^k rounded to the nearest double (ties to even) with integer
 // operations only: the 128-bit two's-complement sum, its leading bit, a 53-bit
 // mantissa with round and sticky bits, and the exponent field; ldexp of the
@@ -339,6 +361,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
       const int mt = t % g.mtiles, nt = t / g.mtiles;
+      if (g.mode != 0) {  // C is read in the final update: start bringing it into L2 now
+        const long long gi = (long long)mt * BM + row;
+        if (gi < g.M)
+#pragma unroll 4
+          for (int j = 0; j < EPI_COLS; ++j) {
+            const long long gj = (long long)nt * BN + col0 + j;
+            if (gj < g.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(g.C + gi + gj * g.ldc));
+          }
+      }
       long long ai[EPI_COLS];  // levels 0-3, in units of level 3
       long long al[EPI_COLS];  // levels 4-7, in units of level 7
 #pragma unroll
@@ -356,45 +387,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
 #pragma unroll
         for (int grp = 0; grp < EPI_COLS / 8; ++grp) {
           const uint32_t cbase = tmem + tlane + (uint32_t)(col0 + grp * 8);
-          float v[8];
-          long long I[8];
           // leading levels: exact integers below 2^24 (32-bit conversions),
           // combined exactly in int64
-          tmem_ld8(cbase, v);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) I[i] = (long long)__float2int_rn(v[i]);
-          for (int l = 1; l < 4; ++l) {
-            if (l < nlev) {
-              tmem_ld8(cbase + (uint32_t)(l * BN), v);
-#pragma unroll
-              for (int i = 0; i < 8; ++i) I[i] = (I[i] << BETA) + (long long)__float2int_rn(v[i]);
-            } else {
-#pragma unroll
-              for (int i = 0; i < 8; ++i) I[i] <<= BETA;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) ai[grp * 8 + i] += I[i];
+          tmem_levels4(cbase, 0, nlev, ai + grp * 8);
           // remaining levels, combined the same way in int64 (their FP32
           // accumulators may exceed 2^24 and round there, far below the
           // result's last bit; the values stay integers below 2^31)
-          if (nlev > 4) {
-            tmem_ld8(cbase + (uint32_t)(4 * BN), v);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) I[i] = (long long)__float2int_rn(v[i]);
-            for (int l = 5; l < 8; ++l) {
-              if (l < nlev) {
-                tmem_ld8(cbase + (uint32_t)(l * BN), v);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) I[i] = (I[i] << BETA) + (long long)__float2int_rn(v[i]);
-              } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) I[i] <<= BETA;
-              }
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) al[grp * 8 + i] += I[i];
-          }
+          if (nlev > 4) tmem_levels4(cbase, 4, nlev, al + grp * 8);
         }
         tc_fence_before();
         __syncwarp();
