@@ -140,6 +140,21 @@ def leaf_families(precision):
     return skip
 
 
+def job_throughput(seconds_this_rank, units_this_rank, dist=None, device="cpu"):
+    """Whole-job rate over replicas: every rank processed units_this_rank in
+    its own seconds_this_rank; the job lasts as long as its slowest rank (max
+    over ranks).  Returns (units of all ranks / that time, that time)."""
+    import torch
+    t = torch.tensor([float(seconds_this_rank)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_s = float(t.item())
+    return world * units_this_rank / max_s, max_s
+
+
 def setup_lib(rfm):
     lib = rfm.load()
     lib.rfm_profile_enable.argtypes = [rfm.ctypes.c_int]
@@ -289,14 +304,9 @@ def run_batch(args, rank, world, local_rank, wl, lib, rfm, dist):
     launches = lib.rfm_launch_count() - l0
     dom_ms, dom_cnt, dom_work = read_dominant(lib, rfm, names, dom_fams)
     lib.rfm_profile_enable(0)
-    total_s = sum(times) / 1e3
-    t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_s = float(t.item())
     cs, infos, tuned = out
     count = len(descs)
-    value = world * count * args.steps / max_s
+    value, max_s = job_throughput(sum(times) / 1e3, count * args.steps, dist, "cuda")
     acc = {"outer_iters_mean": float(np.mean([i["outer_iters"] for i in infos])),
            "n_jac_mean": float(np.mean([i["n_jac"] for i in infos])),
            "lsqr_iters_mean": float(np.mean([i["lsqr_iters_total"] for i in infos]))}
@@ -451,12 +461,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     dom_ms, dom_cnt, dom_work = read_dominant(lib, rfm, names, dom_fams)
     lib.rfm_profile_enable(0)
-    total_s = sum(times) / 1e3
-    t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+    value, max_s = job_throughput(sum(times) / 1e3, args.steps, dist, "cuda")
     if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    max_s = float(t.item())
 
     # accuracy of the last solve
     X = W.eval_grid(desc)
@@ -484,7 +491,6 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = world / statistics.median(e2e_times) if e2e_times else None
 
     steps_per_rank = args.steps
-    value = world * steps_per_rank / max_s
     roof = roofline(dom_fams, dom_ms, dom_cnt, dom_work)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

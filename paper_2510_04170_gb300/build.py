@@ -2,8 +2,8 @@
 
 Each .cu file is compiled to an object in parallel, then linked into a shared
 library with the CUDA runtime linked statically.  Host code is compiled with
-floating-point contraction off so host-side scalar recurrences round exactly as
-written.
+floating-point contraction off so host-side scalar arithmetic (the line search
+bracket, stopping tests) rounds exactly as written.
 """
 import concurrent.futures as cf
 import os

@@ -1,8 +1,9 @@
 // C ABI of librfm: problem set-up, the individual hot-path steps and the IPN /
 // AMIPN drivers (Alg. 1, Alg. 2 of arXiv 2510.04170).  All numerical work runs
-// in the kernels of assemble.cu, sketch.cu, qr.cu and krylov.cu; the host code
-// here only sequences launches and evaluates scalar recurrences (LSQR's plane
-// rotations, the golden-section bracket, the Newton stopping tests).
+// in kernels (here and in assemble.cu, sketch.cu, qr.cu, oz.cu, krylov.cu);
+// LSQR's scalar recurrences run on the device too.  The host code sequences
+// launches and evaluates the golden-section bracket and the Newton stopping
+// tests.
 #include <math.h>
 #include <string.h>
 

@@ -166,7 +166,6 @@ struct rfm_batch {
   std::vector<rfm_problem*> probs;
   std::vector<cudaStream_t> streams;
   std::vector<QrChoice> choice;  // per instance, filled by the autotuner
-  bool tuned = false;
 };
 
 extern "C" {
