@@ -6,8 +6,8 @@ parameters), solver options, and seeded random vectors / query points used by
 tests and the benchmark.  It holds none of the method's arithmetic; both the
 CUDA library and the CPU oracle interpret these descriptors independently.
 
-Problem families (the paper's experiments, Sec. 6; configuration sizes follow
-the workloads named in the benchmark descriptor):
+Problem families (the paper's experiments, Sec. 6; configuration sizes are
+those of the configurations C1-C5 below):
 
   pde_kind 0  -Lap u + u^3 = f,  u* = prod sin(pi x_d)       (Sec. 6.1, Eq. 6.1)
   pde_kind 1  steady Gray-Scott, two fields u, v              (Sec. 6.2, Gray-Scott
