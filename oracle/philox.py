@@ -110,21 +110,38 @@ def round_bf16(x):
     return bits.view(np.float64)
 
 
+def _box_muller_pairs(q, rows, kJ, seed):
+    """Both normals of the Box-Muller pair drawn with counter (2, i, q, kJ)
+    for every pair index q and Jacobian row i: ([len(q), len(rows)], same)."""
+    k0, k1 = seed_key(seed)
+    rows = np.asarray(rows, dtype=np.uint64)
+    q = np.asarray(q, dtype=np.uint64)
+    x0, x1, x2, x3 = philox4x32_10(2, rows[None, :], q[:, None], kJ, k0, k1)
+    u1 = uniform53(x0, x1)
+    u2 = uniform53(x2, x3)
+    rad = np.sqrt(-2.0 * np.log(1.0 - u1))
+    th = 6.283185307179586 * u2
+    return rad * np.cos(th), rad * np.sin(th)
+
+
 def gaussian_sketch(s, rows, kJ, seed):
     """Columns `rows` of the Gaussian sketch S_k (s x m): entry (r, i) is the
     (r mod 2)-th Box-Muller normal of the pair drawn with counter
     (2, i, r div 2, kJ), rounded to the nearest multiple of 2^-4.
     Returns [s, len(rows)]."""
     assert s % 2 == 0
-    k0, k1 = seed_key(seed)
-    rows = np.asarray(rows, dtype=np.uint64)
-    q = np.arange(s // 2, dtype=np.uint64)
-    x0, x1, x2, x3 = philox4x32_10(2, rows[None, :], q[:, None], kJ, k0, k1)
-    u1 = uniform53(x0, x1)
-    u2 = uniform53(x2, x3)
-    rad = np.sqrt(-2.0 * np.log(1.0 - u1))
-    th = 6.283185307179586 * u2
-    out = np.empty((s, rows.size))
-    out[0::2] = rad * np.cos(th)
-    out[1::2] = rad * np.sin(th)
+    c, sn = _box_muller_pairs(np.arange(s // 2), rows, kJ, seed)
+    out = np.empty((s, len(rows)))
+    out[0::2] = c
+    out[1::2] = sn
+    return np.rint(16.0 * out) / 16.0
+
+
+def gaussian_sketch_rows(srows, rows, kJ, seed):
+    """Entries S_k[r, i] for the sketch rows r in `srows` and the Jacobian
+    rows i in `rows` (the same definition as gaussian_sketch, for a few rows
+    of a sketch too large to draw whole).  Returns [len(srows), len(rows)]."""
+    srows = np.asarray(srows, dtype=np.uint64)
+    c, sn = _box_muller_pairs(srows // np.uint64(2), rows, kJ, seed)
+    out = np.where((srows % np.uint64(2) == 0)[:, None], c, sn)
     return np.rint(16.0 * out) / 16.0

@@ -346,3 +346,12 @@ def test_c1_manufactured_solution_converges():
     assert newton.rel_l2(newton.evaluate(p, c2, X), ue) < 1e-6
     assert info2.n_jac < info.n_jac
     assert max(info.lsqr_iters) < 100
+
+
+def test_gaussian_sketch_rows_are_rows_of_the_sketch():
+    """The few-rows form used at full sizes draws the same entries."""
+    from oracle import philox as _ph
+    rows = np.arange(40) + 777
+    S = _ph.gaussian_sketch(96, rows, 2, 20251004)
+    pick = np.array([0, 1, 2, 33, 95, 64])
+    assert np.array_equal(_ph.gaussian_sketch_rows(pick, rows, 2, 20251004), S[pick])
