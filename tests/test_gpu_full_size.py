@@ -102,3 +102,24 @@ def test_sampled_sketch_entries_and_qr_properties(c2):
             gram = float(np.dot(Bc[a].astype(np.longdouble), Bc[b_].astype(np.longdouble)))
             rr = float(np.dot(Rc[a].astype(np.longdouble), Rc[b_].astype(np.longdouble)))
             assert abs(rr - gram) <= 1e-14 * s * na * np.linalg.norm(Bc[b_])
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_c5_instance_solve_matches_oracle(precision):
+    """A whole IPN solve at the C5 size (n = 4,096) against the oracle's solve
+    of the same instance, stored by tests/golden/make_c5_ipn_oracle.py: equal
+    outer iterations, Jacobian evaluations and LSQR steps, and u within 1e-7
+    (relative L2 on the evaluation grid)."""
+    import os
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_04170_gb300 import build, rfm
+    build.build()
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "c5_ipn_oracle.npz"))
+    desc = W.config_c5(*ref["params"])
+    gp = rfm.Problem(desc)
+    c, info = gp.rfm_ipn_solve(W.solve_opts(precision=precision))
+    assert info["outer_iters"] == int(ref["outer_iters"]) and info["n_jac"] == int(ref["n_jac"])
+    assert info["lsqr_iters_total"] == int(ref["lsqr_iters"].sum())
+    u = gp.rfm_eval(c, torch.as_tensor(W.eval_grid(desc), device="cuda")).cpu().numpy()
+    assert np.linalg.norm(u - ref["u"]) <= 1e-7 * np.linalg.norm(ref["u"])
