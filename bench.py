@@ -5,6 +5,7 @@ Workloads (seeded synthetic PDE instances; the paper uses no datasets):
       (n = 32,768), 12^3 interior points and 6x6 per face (m = 124,416),
       Gaussian sketch with 65,536 rows, IPN.
   c1  2D analogue: 2x2 subdomains, M=100, 20x20 points, count sketch gamma=3.
+  c3  3D steady Gray-Scott (two fields), n = 32,768, AMIPN with inner cap 5.
   c4  64 uneven instances (n = 1,024 .. 16,384) solved as one batch per step,
       QR configuration autotuned per instance size.
   c5  128 held-out instances of a parameterised family solved as one batch per
@@ -57,6 +58,11 @@ def workload(name, precision=None, solver=None):
         p = 2 if precision is None else precision
         wl = dict(desc=W.config_c2(), opts=W.opts_c2(precision=p), solver=solver or "ipn", large=True,
                   label="c2: 3D -Lap u+u^3, 4x4x4 subdomains, M=512, n=32768, m=124416, Gaussian sketch s=65536")
+    elif name == "c3":
+        p = 2 if precision is None else precision
+        wl = dict(desc=W.config_c3(), opts=W.solve_opts(precision=p, m_max=5), solver=solver or "amipn", large=True,
+                  label="c3: 3D steady Gray-Scott, 2 fields, 4x4x4 subdomains, M=256 per field, n=32768, m=248832, "
+                        "count sketch s=98304, AMIPN with inner cap 5")
     elif name == "c4":
         p = -1 if precision is None else precision
         wl = dict(descs=W.config_c4_instances(64, seed=1), opts=W.solve_opts(precision=p), solver=solver or "ipn",
