@@ -199,9 +199,14 @@ rfm_status mm(cudaStream_t st, const TA* A, long long sam, long long sak, const 
 
 rfm_status ensure_batch(rfm_mlp* p, int B) {
   if (B <= p->bcap) return RFM_OK;
-  void* bufs[] = {p->x, p->h1, p->h2, p->y, p->dy, p->dh1, p->dh2, p->lossp, p->xb, p->h1b, p->h2b, p->dyb, p->dh2b};
-  for (void* b : bufs)
-    if (b) cudaFree(b);
+  void** bufs[] = {(void**)&p->x,   (void**)&p->h1,  (void**)&p->h2,  (void**)&p->y,   (void**)&p->dy,
+                    (void**)&p->dh1, (void**)&p->dh2, (void**)&p->lossp, (void**)&p->xb, (void**)&p->h1b,
+                    (void**)&p->h2b, (void**)&p->dyb, (void**)&p->dh2b};
+  for (void** b : bufs) {  // no stale pointer survives a failed reallocation
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  p->bcap = 0;
   auto al = [&](void** ptr, size_t bytes) -> bool { return cudaMalloc(ptr, bytes) == cudaSuccess; };
   const size_t fb = sizeof(float), hb = sizeof(__nv_bfloat16);
   const size_t nblk = kLossBlocks;
@@ -323,8 +328,8 @@ rfm_status rfm_mlp_create(int din, int hidden, int dout, uint64_t seed, void* cu
             cudaMalloc((void**)&p->g, o * sizeof(float)) == cudaSuccess &&
             cudaMalloc((void**)&p->wb, o * sizeof(__nv_bfloat16)) == cudaSuccess;
   if (!ok) {
+    rfm_mlp_destroy(p);  // frees whatever was allocated
     rfm_set_error("mlp: allocation failed");
-    delete p;
     return RFM_ENOMEM;
   }
   cudaMemsetAsync(p->w, 0, o * sizeof(float), p->st);
@@ -339,7 +344,8 @@ rfm_status rfm_mlp_create(int din, int hidden, int dout, uint64_t seed, void* cu
     k_init_uniform<<<blocks_for(sz[2 * l]), 256, 0, p->st>>>(p->w + p->off[2 * l], sz[2 * l], sc, (uint32_t)l, k0, k1);
   }
   k_to_bf16<<<blocks_for(o), 256, 0, p->st>>>(p->w, o, p->wb);
-  if (cudaStreamSynchronize(p->st) != cudaSuccess) {
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->st) != cudaSuccess) {
+    rfm_mlp_destroy(p);
     rfm_set_error("mlp: initialisation failed");
     return RFM_ECUDA;
   }
