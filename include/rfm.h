@@ -209,7 +209,12 @@ rfm_status rfm_jmv(rfm_problem* p, int trans, const double* x_dev, double* y_dev
 rfm_status rfm_trsv(rfm_problem* p, int trans, const double* b_dev, double* x_dev);
 
 /* LSQR (Paige-Saunders) on J R^{-1} y ~ b with atol = btol = eta; returns the
- * Newton direction d = R^{-1} y in d_dev [n] (Alg. 1 steps 3-4). */
+ * Newton direction d = R^{-1} y in d_dev [n] (Alg. 1 steps 3-4).  The scalar
+ * recurrences stay on the device; the iterations run in chunks of 16 that the
+ * first call on a problem captures into a CUDA graph (on a private stream of
+ * the problem) and later calls replay on the problem's stream; the graph is
+ * rebuilt when R or the workspace moves.  While per-kernel profiling of the
+ * LSQR kernels is on, the same kernels are launched one by one instead. */
 rfm_status rfm_lsqr(rfm_problem* p, const double* b_dev, double eta, double conlim, int64_t max_iter,
                     double* d_dev, int* iters_host, int* istop_host);
 
@@ -219,7 +224,11 @@ rfm_status rfm_linesearch(rfm_problem* p, const double* c_dev, const double* d_d
                           double* alpha_host, double* fbest_host);
 
 /* IPN (Alg. 1) and AMIPN (Alg. 2) from the initial guess in c_dev [n]
- * (overwritten with the result).  info (nullable) is filled. */
+ * (overwritten with the result).  info (nullable) is filled.  AMIPN follows
+ * Alg. 2 as printed: an early stop of the inner loop keeps J~ and R for the
+ * next outer iteration, so from a poor guess it can stop on a stale Jacobian
+ * (a steady Gray-Scott system from u_0 = 0 does); IPN re-linearises at every
+ * step. */
 rfm_status rfm_ipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_dev, rfm_solve_info* info);
 rfm_status rfm_amipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_dev, rfm_solve_info* info);
 
