@@ -355,3 +355,26 @@ def test_gaussian_sketch_rows_are_rows_of_the_sketch():
     S = _ph.gaussian_sketch(96, rows, 2, 20251004)
     pick = np.array([0, 1, 2, 33, 95, 64])
     assert np.array_equal(_ph.gaussian_sketch_rows(pick, rows, 2, 20251004), S[pick])
+
+
+def test_amipn_as_printed_keeps_a_stale_jacobian():
+    """Alg. 2 recomputes the preconditioned Jacobian only when the inner loop
+    runs to m_max; an early inner stop keeps it.  On a steady Gray-Scott system
+    from u_0 = 0 the inner loop stops early with the Jacobian of u_0 and the
+    outer test then ends the solve on that one Jacobian, well short of what
+    IPN (a fresh Jacobian every step) reaches.  The GPU solver shows the same
+    behaviour at full size; this records the reading."""
+    from oracle import newton as _nt
+    desc = W.small_3d(pde_kind=1, fields=2, M=20)
+    op = Problem(desc)
+    X = W.eval_grid(desc, per_axis=4)
+    ue = op.exact(X)
+    err = {}
+    nj = {}
+    for solver in ("amipn", "ipn"):
+        c, info = getattr(_nt, solver)(op, W.solve_opts(m_max=5))
+        u = _nt.evaluate(op, c, X)
+        err[solver] = np.linalg.norm(u - ue) / np.linalg.norm(ue)
+        nj[solver] = info.n_jac
+    assert nj["amipn"] == 1 and nj["ipn"] > 5
+    assert err["amipn"] > 2 * err["ipn"]
