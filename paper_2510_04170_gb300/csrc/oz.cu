@@ -30,9 +30,11 @@
 //           (kind::f16, bf16 x bf16 -> f32, M=128, N=64, K=16) for every digit
 //           pair into the TMEM accumulator of its level (64 columns each) and
 //           commits to mbarriers
-//   warps 2-9 epilogue: tcgen05.ld the levels of each chunk, combine, keep
-//           the running sums in registers (two warps per TMEM lane quarter,
-//           32 columns each), scale and write C
+//   warps 2-9 epilogue: tcgen05.ld the levels of each chunk, combine them
+//           into two int64 running sums per element (two warps per TMEM
+//           lane quarter, 32 columns each), then round once to FP64, scale
+//           and write (or subtract from) C; C is prefetched into L2 at the
+//           start of the tile and read-modify-written four columns at a time
 // Digit tiles are K-major with 128-byte rows in the 128B-swizzle pattern so a
 // tile is one contiguous bulk copy and the UMMA shared-memory descriptor reads
 // it directly.  Every wait is bounded; on timeout an error word is set, the
