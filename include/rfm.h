@@ -114,10 +114,13 @@ const char* rfm_last_error(void);
 rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, rfm_problem** out);
 rfm_status rfm_problem_destroy(rfm_problem* p);
 
-/* m rows, n unknowns, W = fields*M (width of a column block), G subdomains,
- * m_int / m_iface interior and interface row counts. */
+/* Sizes of the least-squares system F: R^n -> R^m of Sec. 3.2 (m = Q_I + Q_b
+ * + Q_c rows): m rows, n unknowns, W = fields*M (width of a column block), G
+ * subdomains, m_int / m_iface interior and interface row counts, and nnz the
+ * stored Jacobian entries ((m + m_iface) * W: one W-wide block per row plus
+ * the second block of each interface row).  Null outputs are skipped. */
 rfm_status rfm_problem_sizes(const rfm_problem* p, int64_t* m, int64_t* n, int64_t* W,
-                             int64_t* G, int64_t* m_int, int64_t* m_iface);
+                             int64_t* G, int64_t* m_int, int64_t* m_iface, int64_t* nnz);
 
 /* Copies the feature table [G*fields*M][4] (k_1..k_d, b, zero padding) and
  * the row points [m][4] (x_1..x_d, padding) to device buffers (Sec. 2.2). */
@@ -130,10 +133,12 @@ rfm_status rfm_get_points(const rfm_problem* p, double* pts_dev);
  * lam_dev [m] (nullable) the row scales. */
 rfm_status rfm_assemble(rfm_problem* p, const double* c_dev, double c_scale, double* F_dev, double* lam_dev);
 
-/* Copies the stored scaled Jacobian: Jp_dev [m][W] holds each row's primary
- * block (columns of subdomain e0), Js_dev [m_iface][W] the secondary block of
- * interface rows (subdomain e1); blk_dev (int32 [m][2], nullable) gets
- * (e0, e1) with e1 = -1 for non-interface rows. */
+/* Copies the stored scaled Jacobian J = [lambda A_int + mu dg/du; A_con;
+ * A_bdy] (Sec. 5, rows scaled by lambda_i): Jp_dev [m][W] holds each row's
+ * primary block (columns of subdomain e0), Js_dev [m_iface][W] the secondary
+ * block of interface rows (subdomain e1); blk_dev (int32 [m][2], nullable)
+ * gets (e0, e1) with e1 = -1 for non-interface rows.  RFM_EINVAL before the
+ * first rfm_assemble. */
 rfm_status rfm_get_jacobian(const rfm_problem* p, double* Jp_dev, double* Js_dev, int32_t* blk_dev);
 
 /* Scaled residual W F(c) with the stored row scales (no Jacobian).  F_dev [m]
@@ -141,11 +146,22 @@ rfm_status rfm_get_jacobian(const rfm_problem* p, double* Jp_dev, double* Js_dev
 rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, double* norm_host);
 
 /* Sketch of the stored scaled J for Jacobian evaluation kJ (Sec. 4.1):
- * count sketch (B[h(i),:] += sigma(i) J[i,:]) or Gaussian sketch with
- * bfloat16-exact N(0,1) entries.  s rows; B kept inside the problem as an
- * s x n column-major matrix.  B_dev (nullable, [n][s] column-major) receives a
- * copy. */
+ * count sketch (B[h(i),:] += sigma(i) J[i,:]) or Gaussian sketch whose
+ * entries are N(0,1) draws rounded to multiples of 2^-4 (each an integer of
+ * magnitude <= 137 times 2^-4, exact in bfloat16).  s rows; B kept inside the
+ * problem as an s x n column-major matrix.  B_dev (nullable, [n][s]
+ * column-major) receives a copy. */
 rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev);
+
+/* Limit on the device-side polls of the bounded flag waits (the grid barriers
+ * of the QR panel factorisation and the block flags of the triangular solves)
+ * of this problem: 0 restores the default (2^22 polls), a positive count sets
+ * that many, a negative value makes every such wait give up at once (for
+ * testing the RFM_ETIMEOUT path).  A wait that gives up sets the problem's
+ * error word; the call reports RFM_ETIMEOUT and its result is invalid, and
+ * the next call starts with a clear error word.  The paper has no
+ * counterpart (failure detection of this library). */
+rfm_status rfm_set_wait_limit(rfm_problem* p, int64_t polls);
 
 /* Precision level (see rfm_solve_opts.precision) used by rfm_sketch and
  * rfm_qr; the solvers set it from their options.  RFM_EINVAL outside 0..2. */
@@ -156,7 +172,9 @@ rfm_status rfm_set_precision(rfm_problem* p, int precision);
  * as the preconditioner.  R_dev (nullable, [n][n] column-major) receives R. */
 rfm_status rfm_qr(rfm_problem* p, double* R_dev);
 
-/* Installs a caller-supplied preconditioner R (n x n column-major upper). */
+/* Installs a caller-supplied right preconditioner R (Sec. 4.1: the R factor
+ * of the sketch, used as J R^{-1} in Alg. 1 step 3), n x n column-major upper
+ * triangular, copied into a buffer the problem owns. */
 rfm_status rfm_set_r(rfm_problem* p, const double* R_dev);
 
 /* Standalone Householder R of an s x n column-major matrix (ld = s), the same
@@ -202,10 +220,14 @@ rfm_status rfm_householder_r_noalloc(double* A_dev, int64_t s, int64_t n, void* 
                                      int* rank_flag_host);
 
 /* y = J x (trans 0, x [n], y [m]) or y = J^T x (trans 1, x [m], y [n]) with
- * the stored scaled J. */
+ * the stored scaled J: the products of the bidiagonalisation that LSQR
+ * applies to J R^{-1} (Alg. 1 step 3). */
 rfm_status rfm_jmv(rfm_problem* p, int trans, const double* x_dev, double* y_dev);
 
-/* x = R^{-1} b (trans 0) or x = R^{-T} b (trans 1) with the stored R. */
+/* x = R^{-1} b (trans 0) or x = R^{-T} b (trans 1) with the stored R: the
+ * preconditioner solves inside LSQR on J R^{-1} and the back-transformation
+ * of the Newton direction d = R^{-1} y (Alg. 1 steps 3-4).  RFM_ETIMEOUT if a
+ * bounded device wait gave up (x is then invalid). */
 rfm_status rfm_trsv(rfm_problem* p, int trans, const double* b_dev, double* x_dev);
 
 /* LSQR (Paige-Saunders) on J R^{-1} y ~ b with atol = btol = eta; returns the

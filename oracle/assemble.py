@@ -13,6 +13,14 @@ sigma_e (Sec. 2.2, Eq. 2.6), with the analytic derivatives
 
 Operators (pde_kind):
   0  F = -Lap u + p0 u^3 - f                 J = -Lap phi + 3 p0 u^2 phi
+  4  F = Lap u + p0 u + p1 cosh(u) - f        J = Lap phi + (p0 + p1 sinh u) phi
+     (nonlinear Helmholtz of Sec. 6.2, p0 = -100, p1 = 10)
+  5  F = -div((1 + u^2) grad u) - f = -(1 + u^2) Lap u - 2 u |grad u|^2 - f
+     J = -(1 + u^2) Lap phi - (2 u Lap u + 2 |grad u|^2) phi - 4 u grad u . grad phi
+     (Sec. 3.2 benchmark)
+  6  F = -div((1 + |grad u|^2) grad u) - f = -(1 + |g|^2) Lap u - 2 g^T H g - f
+     J = -(1 + |g|^2) Lap phi - 2 Lap u (g . grad phi) - 4 grad phi . H g - 2 g^T Hess(phi) g
+     (strongly nonlinear example of Sec. 6.2; g = grad u, H = Hess u)
   2,3 F = -a Lap u - a_x u_x + kap u^3 - f    J = -a Lap phi - a_x phi_x + 3 kap u^2 phi
       with a = 1 + 0.5 sin(2 pi x), a_x = pi cos(2 pi x)
   1  (Gray-Scott, fields u, v)
@@ -52,6 +60,21 @@ def feature_values(prob, e_arr, X):
     for b in range(d):
         lap = lap + (-2.0 * T * S1) * ks[..., b] ** 2
     return T, grad, lap
+
+
+def feature_hessian(prob, e_arr, X):
+    """Second derivatives d^2 phi / dx_a dx_b = -2 t (1 - t^2) (k_a / sigma_a)
+    (k_b / sigma_b) of every feature, shape (r, fields, M, d, d)."""
+    d = prob.d
+    sg = prob.sigma[e_arr]
+    L = (X - prob.mu[e_arr]) / sg
+    K = prob.feats[e_arr, :, :, :d]
+    Z = prob.feats[e_arr, :, :, d].copy()
+    for b in range(d):
+        Z = Z + L[:, b, None, None] * K[..., b]
+    T = np.tanh(Z)
+    ks = K / sg[:, None, None, :]
+    return (-2.0 * T * (1.0 - T * T))[..., None, None] * ks[..., :, None] * ks[..., None, :]
 
 
 def _coef_block(prob, c, e_arr):
@@ -114,6 +137,40 @@ def assemble_rows(prob, c, rows, want_jacobian=True):
                 Jv_v = -ev * lap[:, 1] + (-2.0 * uu * vv + (Fc + kk))[:, None] * phi[:, 1]
                 Jp[sel[t0], :M] = Ju_u[t0]; Jp[sel[t0], M:] = Ju_v[t0]
                 Jp[sel[t1], :M] = Jv_u[t1]; Jp[sel[t1], M:] = Jv_v[t1]
+        elif k in (4, 5, 6):
+            # 3D examples of Sec. 6.2 (one field), from the 2-jet of u at the point
+            phi0, grad0, lap0 = phi[:, 0], grad[:, 0], lap[:, 0]
+            cb0 = cb[:, 0]
+            uu = u[:, 0]
+            lu0 = lu[:, 0]
+            gu = np.einsum("rmb,rm->rb", grad0, cb0)           # grad u
+            gg = np.einsum("rb,rb->r", gu, gu)                  # |grad u|^2
+            if k == 4:
+                # Lap u + p0 u + p1 cosh(u) = f
+                F[sel] = lu0 + p[0] * uu + p[1] * np.cosh(uu) - src
+                if want_jacobian:
+                    Jp[sel, :M] = lap0 + (p[0] + p[1] * np.sinh(uu))[:, None] * phi0
+            elif k == 5:
+                # -div((1 + u^2) grad u) = -(1 + u^2) Lap u - 2 u |grad u|^2
+                F[sel] = -(1.0 + uu * uu) * lu0 - 2.0 * uu * gg - src
+                if want_jacobian:
+                    gphi = np.einsum("rmb,rb->rm", grad0, gu)       # grad u . grad phi_j
+                    Jp[sel, :M] = (-(1.0 + uu * uu)[:, None] * lap0
+                                   - (2.0 * uu * lu0 + 2.0 * gg)[:, None] * phi0
+                                   - (4.0 * uu)[:, None] * gphi)
+            else:
+                # -div((1 + |grad u|^2) grad u) = -(1 + |g|^2) Lap u - 2 g^T H g
+                hess0 = feature_hessian(prob, e0[sel], X[sel])[:, 0]       # (r, M, d, d)
+                Hu = np.einsum("rmab,rm->rab", hess0, cb0)
+                Hg = np.einsum("rab,rb->ra", Hu, gu)
+                gHg = np.einsum("ra,ra->r", gu, Hg)
+                F[sel] = -(1.0 + gg) * lu0 - 2.0 * gHg - src
+                if want_jacobian:
+                    gphi = np.einsum("rmb,rb->rm", grad0, gu)
+                    hphi = np.einsum("rmb,rb->rm", grad0, Hg)          # grad phi_j . H g
+                    gHphig = np.einsum("ra,rmab,rb->rm", gu, hess0, gu)
+                    Jp[sel, :M] = (-(1.0 + gg)[:, None] * lap0 - (2.0 * lu0)[:, None] * gphi
+                                   - 4.0 * hphi - 2.0 * gHphig)
         else:
             raise ValueError(k)
     # interface rows: [d^s phi_e0 | -d^s phi_e1] on the row's field

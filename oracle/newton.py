@@ -106,13 +106,23 @@ def scaled_norm(prob, lam, c):
     return float(np.linalg.norm(lam * asm.residual(prob, c)))
 
 
-def ipn(prob, opts, c0=None, blocked=True):
-    """Algorithm 1 (IPN)."""
+def _make_lin(prob, opts, c, kJ, blocked, lean, workers):
+    if lean:
+        from .lean import LeanLin
+        return LeanLin(prob, opts, c, kJ, workers)
+    return _Lin(prob, opts, c, kJ, blocked)
+
+
+def ipn(prob, opts, c0=None, blocked=True, lean=False, workers=0, log=None):
+    """Algorithm 1 (IPN).  lean=True keeps J in block form and forms the
+    sketch and QR without dense m x n or s x m arrays (oracle.lean); workers
+    spreads the Gaussian sketch over that many processes; log(k, info) is
+    called after each outer iteration."""
     n = prob.n
     c = np.zeros(n) if c0 is None else np.array(c0, dtype=np.float64)
     info = Info()
     for k in range(int(opts["max_outer"])):
-        lin = _Lin(prob, opts, c, k, blocked)
+        lin = _make_lin(prob, opts, c, k, blocked, lean, workers)
         info.n_jac += 1
         info.rank_flag |= lin.rank_flag
         f0 = scaled_norm(prob, lin.lam, c)
@@ -123,12 +133,14 @@ def ipn(prob, opts, c0=None, blocked=True):
         c = c + alpha * d
         info.outer_iters = k + 1
         info.final_resid = f1
+        if log is not None:
+            log(k, info)
         if abs(f1 - f0) < opts["eps"]:
             break
     return c, info
 
 
-def amipn(prob, opts, c0=None, blocked=True):
+def amipn(prob, opts, c0=None, blocked=True, lean=False, workers=0, log=None):
     """Algorithm 2 (AMIPN): one Jacobian and preconditioner per outer
     iteration, up to m_max inner steps reusing them, early stop when
     ||F_{k,i+1} - F_{k,i}|| < tau_rel ||F_{k,0}||; the Jacobian is recomputed
@@ -137,7 +149,7 @@ def amipn(prob, opts, c0=None, blocked=True):
     c = np.zeros(n) if c0 is None else np.array(c0, dtype=np.float64)
     info = Info()
     kJ = 0
-    lin = _Lin(prob, opts, c, kJ, blocked)
+    lin = _make_lin(prob, opts, c, kJ, blocked, lean, workers)
     info.n_jac = 1
     info.rank_flag |= lin.rank_flag
     for k in range(int(opts["max_outer"])):
@@ -163,11 +175,13 @@ def amipn(prob, opts, c0=None, blocked=True):
         info.outer_iters = k + 1
         nk1 = float(np.linalg.norm(Fprev))
         info.final_resid = nk1
+        if log is not None:
+            log(k, info)
         if abs(nk1 - nk0) < opts["eps"]:
             break
         if flag:
             kJ += 1
-            lin = _Lin(prob, opts, c, kJ, blocked)
+            lin = _make_lin(prob, opts, c, kJ, blocked, lean, workers)
             info.n_jac += 1
             info.rank_flag |= lin.rank_flag
     return c, info

@@ -130,8 +130,15 @@ def gaussian_sketch(s, rows, kJ, seed):
     (2, i, r div 2, kJ), rounded to the nearest multiple of 2^-4.
     Returns [s, len(rows)]."""
     assert s % 2 == 0
-    c, sn = _box_muller_pairs(np.arange(s // 2), rows, kJ, seed)
-    out = np.empty((s, len(rows)))
+    return gaussian_sketch_range(0, s, rows, kJ, seed)
+
+
+def gaussian_sketch_range(r0, r1, rows, kJ, seed):
+    """Rows r0 <= r < r1 (both even) of the Gaussian sketch S_k, columns
+    `rows`, by the definition of gaussian_sketch.  Returns [r1 - r0, len(rows)]."""
+    assert r0 % 2 == 0 and r1 % 2 == 0 and r1 >= r0
+    c, sn = _box_muller_pairs(np.arange(r0 // 2, r1 // 2), rows, kJ, seed)
+    out = np.empty((r1 - r0, len(rows)))
     out[0::2] = c
     out[1::2] = sn
     return np.rint(16.0 * out) / 16.0

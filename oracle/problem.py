@@ -146,7 +146,79 @@ class Problem:
             x, y, z = X[:, 0], X[:, 1], X[:, 2]
             u = np.sin(x * (1 - x)) * np.sin(y * (1 - y)) * np.exp(z)
             return np.stack([u, S], axis=1)
+        if k in (4, 5, 6):
+            return self.exact_jet(X)[0][:, None]
         return np.full((X.shape[0], 1), np.nan)
+
+    def exact_jet(self, X):
+        """Value, gradient [npts, 3] and Hessian [npts, 3, 3] of the manufactured
+        solutions of the 3D examples of Sec. 6.2:
+          kind 4 (nonlinear Helmholtz)   u = (2 + x^2 + y^2 + z^2) sin(pi x) sin(pi y) sin(pi z)
+          kind 5 (Lambda(u) = 1 + u^2)   u = (x + y + z) sin(pi x) sin(pi y) cos(pi z)   (Sec. 3.2)
+          kind 6 (Lambda = 1 + |grad u|^2) u = sin(x(1-x)) sin(y(1-y)) e^(z + 1/2)
+        Each is a product form; the derivatives are written out by hand."""
+        pi = math.pi
+        x = [X[:, b] for b in range(3)]
+        npts = X.shape[0]
+        if self.kind == 6:
+            # u = A(x) B(y) C(z), A = sin(x(1-x)), C = e^(z+1/2)
+            fs = []
+            for b in range(2):
+                w = x[b] * (1 - x[b])
+                f0 = np.sin(w)
+                f1 = np.cos(w) * (1 - 2 * x[b])
+                f2 = -np.sin(w) * (1 - 2 * x[b]) ** 2 - 2 * np.cos(w)
+                fs.append((f0, f1, f2))
+            e = np.exp(x[2] + 0.5)
+            fs.append((e, e, e))
+            u = fs[0][0] * fs[1][0] * fs[2][0]
+            g = np.zeros((npts, 3))
+            H = np.zeros((npts, 3, 3))
+            for a in range(3):
+                for b in range(3):
+                    prod = np.ones(npts)
+                    for c in range(3):
+                        order = (a == c) + (b == c)
+                        prod = prod * fs[c][order]
+                    H[:, a, b] = prod
+                prod = np.ones(npts)
+                for c in range(3):
+                    prod = prod * fs[c][1 if c == a else 0]
+                g[:, a] = prod
+            return u, g, H
+        # u = r(x) P(x): P a product of sines (and a cosine for kind 5)
+        trig = []
+        for b in range(3):
+            if self.kind == 5 and b == 2:
+                trig.append((np.cos(pi * x[b]), -pi * np.sin(pi * x[b]), -pi * pi * np.cos(pi * x[b])))
+            else:
+                trig.append((np.sin(pi * x[b]), pi * np.cos(pi * x[b]), -pi * pi * np.sin(pi * x[b])))
+        P = trig[0][0] * trig[1][0] * trig[2][0]
+        dP = np.zeros((npts, 3))
+        HP = np.zeros((npts, 3, 3))
+        for a in range(3):
+            for b in range(3):
+                prod = np.ones(npts)
+                for c in range(3):
+                    prod = prod * trig[c][(a == c) + (b == c)]
+                HP[:, a, b] = prod
+            prod = np.ones(npts)
+            for c in range(3):
+                prod = prod * trig[c][1 if c == a else 0]
+            dP[:, a] = prod
+        if self.kind == 4:
+            r = 2.0 + x[0] ** 2 + x[1] ** 2 + x[2] ** 2
+            dr = np.stack([2 * x[0], 2 * x[1], 2 * x[2]], axis=1)
+            Hr = np.broadcast_to(2.0 * np.eye(3), (npts, 3, 3))
+        else:
+            r = x[0] + x[1] + x[2]
+            dr = np.ones((npts, 3))
+            Hr = np.zeros((npts, 3, 3))
+        u = r * P
+        g = dr * P[:, None] + r[:, None] * dP
+        H = (Hr * P[:, None, None] + dr[:, :, None] * dP[:, None, :] + dP[:, :, None] * dr[:, None, :]
+             + r[:, None, None] * HP)
+        return u, g, H
 
     def source(self, X, f):
         """Right-hand side f of the PDE for field f at interior points."""
@@ -169,6 +241,16 @@ class Problem:
             for b in range(d):
                 S = S * np.sin(q * pi * X[:, b])
             return A * S
+        if k in (4, 5, 6):
+            u, g, H = self.exact_jet(X)
+            lap = H[:, 0, 0] + H[:, 1, 1] + H[:, 2, 2]
+            if k == 4:  # Lap u + p0 u + p1 cosh(u) = f
+                return lap + p[0] * u + p[1] * np.cosh(u)
+            if k == 5:  # -div((1 + u^2) grad u) = -(1 + u^2) Lap u - 2 u |grad u|^2
+                return -(1.0 + u * u) * lap - 2.0 * u * np.einsum("ra,ra->r", g, g)
+            # -div((1 + |grad u|^2) grad u) = -(1 + |g|^2) Lap u - 2 g^T H g
+            gg = np.einsum("ra,ra->r", g, g)
+            return -(1.0 + gg) * lap - 2.0 * np.einsum("ra,rab,rb->r", g, H, g)
         if k == 1:
             eu, ev, F, kk = p[0], p[1], p[2], p[3]
             x, y, z = X[:, 0], X[:, 1], X[:, 2]

@@ -245,6 +245,13 @@ rfm_status read_scalars(rfm_problem* p, const double* dev, int count, double* ho
   return RFM_OK;
 }
 
+// Clears the device error word at the start of a public call, so a wait that
+// gave up in an earlier call is not reported again.
+rfm_status clear_err(rfm_problem* p) {
+  RFM_CUDA(cudaMemsetAsync(p->sync + SYNC_ERR, 0, sizeof(unsigned int), p->stream));
+  return RFM_OK;
+}
+
 rfm_status check_timeout(rfm_problem* p) {
   unsigned int e = 0;
   RFM_CUDA(cudaMemcpyAsync(&e, p->sync + SYNC_ERR, sizeof(unsigned int), cudaMemcpyDeviceToHost, p->stream));
@@ -492,16 +499,15 @@ rfm_status lsqr_graph(rfm_problem* p, double* lst, int* done) {
   // capture on a private stream (the problem's may be the legacy default
   // stream, which cannot be captured); the graph is replayed on p->stream
   if (!p->cap_stream) RFM_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
-  const long long before = rfm_launches_now();
   cudaGraph_t g = nullptr;
   cudaStream_t home = p->stream;
   p->stream = p->cap_stream;
+  rfm_count_pause(true);  // captured launches do not run; this thread stops counting them
   cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
   rfm_status r = e == cudaSuccess ? lsqr_chunk(p, lst, done) : RFM_ECUDA;
   if (e == cudaSuccess) e = cudaStreamEndCapture(p->stream, &g);
+  rfm_count_pause(false);
   p->stream = home;
-  const long long captured = rfm_launches_now() - before;
-  rfm_count_launches(-captured);  // captured, not run
   if (r != RFM_OK) {
     if (g) cudaGraphDestroy(g);
     return r;
@@ -509,6 +515,17 @@ rfm_status lsqr_graph(rfm_problem* p, double* lst, int* done) {
   if (e != cudaSuccess) {
     g_err = std::string("lsqr graph capture: ") + cudaGetErrorString(e);
     return RFM_ECUDA;
+  }
+  // kernels per replay, counted on the captured graph itself
+  size_t nodes = 0;
+  long long kernels = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nodes) == cudaSuccess && nodes > 0) {
+    std::vector<cudaGraphNode_t> list(nodes);
+    if (cudaGraphGetNodes(g, list.data(), &nodes) == cudaSuccess)
+      for (size_t i = 0; i < nodes; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(list[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
   }
   cudaGraphExec_t ex = nullptr;
   e = cudaGraphInstantiate(&ex, g, 0);
@@ -519,7 +536,7 @@ rfm_status lsqr_graph(rfm_problem* p, double* lst, int* done) {
   }
   p->lsqr_graph = ex;
   p->lsqr_graph_key = key;
-  p->lsqr_graph_launches = captured;
+  p->lsqr_graph_launches = kernels;
   return RFM_OK;
 }
 
@@ -693,6 +710,22 @@ rfm_status scaled_residual_norm(rfm_problem* p, const double* c, double* Fout, d
   return read_scalars(p, p->red + 1024 + 16, 1, norm);
 }
 
+// R (upper triangle of the s x n column-major A) into R_dev [n][n]
+// column-major, zeros below; synchronises the stream.  Errors are returned,
+// never thrown past the caller's frees.
+rfm_status copy_r_out(const double* A, long long lda, long long n, double* R_dev, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
+  k_copy_r<<<grid, 256, 0, st>>>(A, lda, n, R_dev);
+  rfm_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    g_err = std::string("householder: ") + cudaGetErrorString(e);
+    return RFM_ECUDA;
+  }
+  return RFM_OK;
+}
+
 bool validate_opts(const rfm_solve_opts* o) {
   return o && (o->sketch_kind == RFM_SKETCH_COUNT || o->sketch_kind == RFM_SKETCH_GAUSS) && o->eta > 0 &&
          o->precision >= 0 && o->precision <= 2 &&
@@ -859,8 +892,9 @@ rfm_status rfm_problem_destroy(rfm_problem* p) {
 }
 
 rfm_status rfm_problem_sizes(const rfm_problem* p, int64_t* m, int64_t* n, int64_t* W, int64_t* G, int64_t* m_int,
-                             int64_t* m_iface) {
+                             int64_t* m_iface, int64_t* nnz) {
   if (!p) return RFM_EINVAL;
+  if (nnz) *nnz = (p->m + p->m_iface) * (int64_t)p->W;
   if (m) *m = p->m;
   if (n) *n = p->n;
   if (W) *W = p->W;
@@ -930,6 +964,17 @@ rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, doub
   return RFM_OK;
 }
 
+rfm_status rfm_set_wait_limit(rfm_problem* p, int64_t polls) {
+  if (!p) {
+    g_err = "rfm_set_wait_limit: null problem";
+    return RFM_EINVAL;
+  }
+  const int v = polls < 0 ? -1 : (int)std::min<int64_t>(polls, 0x7fffffff);
+  RFM_CUDA(cudaMemcpyAsync(p->sync + SYNC_WAITLIM, &v, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  RFM_CUDA(cudaStreamSynchronize(p->stream));
+  return RFM_OK;
+}
+
 rfm_status rfm_set_precision(rfm_problem* p, int precision) {
   if (!p || precision < 0 || precision > 2) {
     g_err = "rfm_set_precision: precision must be 0, 1 or 2";
@@ -941,6 +986,7 @@ rfm_status rfm_set_precision(rfm_problem* p, int precision) {
 
 rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev) {
   if (!p) return RFM_EINVAL;
+  RFM_TRY(clear_err(p));
   RFM_TRY(do_sketch(p, kind, s, kJ));
   p->have_r = false;
   if (B_dev) RFM_CUDA(cudaMemcpyAsync(B_dev, p->B, (size_t)s * p->n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
@@ -953,6 +999,7 @@ rfm_status rfm_qr(rfm_problem* p, double* R_dev) {
     g_err = "rfm_qr: no sketch";
     return RFM_EINVAL;
   }
+  RFM_TRY(clear_err(p));
   RFM_TRY(do_qr(p));
   if (R_dev) {
     dim3 grid((unsigned)std::min<long long>(64, (p->n + 255) / 256), (unsigned)p->n);
@@ -989,12 +1036,7 @@ rfm_status rfm_householder_r(double* A_dev, int64_t s, int64_t n, void* cuda_str
   int flag = 0;
   if (r == RFM_OK && cudaMemsetAsync(sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st) != cudaSuccess) r = RFM_ECUDA;
   if (r == RFM_OK) r = rfm_householder_inplace(A_dev, s, n, s, st, scratch, qs, sync, &flag);
-  if (r == RFM_OK) {
-    dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
-    k_copy_r<<<grid, 256, 0, st>>>(A_dev, s, n, R_dev);
-    RFM_CHECK_LAUNCH();
-    if (cudaStreamSynchronize(st) != cudaSuccess) r = RFM_ECUDA;
-  }
+  if (r == RFM_OK) r = copy_r_out(A_dev, s, n, R_dev, st);
   cudaStreamSynchronize(st);
   dfree(sync);
   dfree(scratch);
@@ -1020,12 +1062,7 @@ rfm_status rfm_householder_r_tc(double* A_dev, int64_t s, int64_t n, void* cuda_
   int flag = 0;
   if (r == RFM_OK && cudaMemsetAsync(sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), st) != cudaSuccess) r = RFM_ECUDA;
   if (r == RFM_OK) r = rfm_householder_emulated(A_dev, s, n, s, st, scratch, qs, sync, emu, eb, &flag);
-  if (r == RFM_OK) {
-    dim3 grid((unsigned)std::min<long long>(64, (n + 255) / 256), (unsigned)n);
-    k_copy_r<<<grid, 256, 0, st>>>(A_dev, s, n, R_dev);
-    rfm_count_launch();
-    if (cudaStreamSynchronize(st) != cudaSuccess) r = RFM_ECUDA;
-  }
+  if (r == RFM_OK) r = copy_r_out(A_dev, s, n, R_dev, st);
   cudaStreamSynchronize(st);
   dfree(sync);
   dfree(emu);
@@ -1043,6 +1080,7 @@ rfm_status rfm_jmv(rfm_problem* p, int trans, const double* x_dev, double* y_dev
 
 rfm_status rfm_trsv(rfm_problem* p, int trans, const double* b_dev, double* x_dev) {
   if (!p || !p->have_r || !b_dev || !x_dev) return RFM_EINVAL;
+  RFM_TRY(clear_err(p));
   RFM_TRY(rfm_launch_trsv(p, trans, b_dev, x_dev));
   return check_timeout(p);
 }
@@ -1050,6 +1088,7 @@ rfm_status rfm_trsv(rfm_problem* p, int trans, const double* b_dev, double* x_de
 rfm_status rfm_lsqr(rfm_problem* p, const double* b_dev, double eta, double conlim, int64_t max_iter, double* d_dev,
                     int* iters_host, int* istop_host) {
   if (!p || !p->have_j || !p->have_r || !b_dev || !d_dev || !(eta > 0)) return RFM_EINVAL;
+  RFM_TRY(clear_err(p));
   LsqrOut lo;
   RFM_TRY(lsqr(p, b_dev, eta, conlim, max_iter > 0 ? max_iter : 2 * p->n, d_dev, &lo));
   if (iters_host) *iters_host = lo.itn;
@@ -1075,6 +1114,7 @@ rfm_status rfm_ipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_d
   rfm_solve_info info;
   memset(&info, 0, sizeof(info));
   p->precision = opts->precision;
+  RFM_TRY(clear_err(p));
   const long long n = p->n, m = p->m;
   double* b = wv(p, WV_B);
   double* d = wv(p, WV_D);
@@ -1108,7 +1148,6 @@ rfm_status rfm_ipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c_d
       }
     }
   }
-  if (st == RFM_OK && info.rank_flag) st = RFM_OK;  // rank floor is reported in info, not as failure
   RFM_CUDA(cudaStreamSynchronize(p->stream));
   info.status = st;
   if (info_out) *info_out = info;
@@ -1124,6 +1163,7 @@ rfm_status rfm_amipn_solve(rfm_problem* p, const rfm_solve_opts* opts, double* c
   rfm_solve_info info;
   memset(&info, 0, sizeof(info));
   p->precision = opts->precision;
+  RFM_TRY(clear_err(p));
   const long long n = p->n, m = p->m;
   double* d = wv(p, WV_D);
   double* z = wv(p, WV_Z);

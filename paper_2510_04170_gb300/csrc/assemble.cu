@@ -497,16 +497,12 @@ rfm_status rfm_launch_setup(rfm_problem* p) {
   k_points<<<grid_for(p->m, 256, 1 << 30), 256, 0, p->stream>>>(
       p->segs, p->nseg, p->X, p->nmaxbp, pc, p->N[0], p->N[1], p->N[2], nullptr, p->pts, p->rmeta, p->rhs, p->m);
   RFM_CHECK_LAUNCH();
-  static const cudaError_t attr = [] {  // once, thread-safe
+  {  // once per device
     const int bytes = 4 * 2 * RFM_MAX_WIDTH * (int)sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_assemble<MODE_JF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_assemble<MODE_RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_assemble<MODE_LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-  }();
-  RFM_CUDA(attr);
+    RFM_CUDA(rfm_smem_attr((const void*)k_assemble<MODE_JF>, bytes));
+    RFM_CUDA(rfm_smem_attr((const void*)k_assemble<MODE_RES>, bytes));
+    RFM_CUDA(rfm_smem_attr((const void*)k_assemble<MODE_LS>, bytes));
+  }
   return RFM_OK;
 }
 

@@ -637,9 +637,7 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
     rfm_set_error("oz_gemm: bad digit counts");
     return RFM_EINVAL;
   }
-  static const cudaError_t attr =  // once, thread-safe
-      cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-  RFM_CUDA(attr);
+  RFM_CUDA(rfm_smem_attr((const void*)k_oz_gemm, (int)oz_smem_bytes()));  // once per device
   OzArgs a;
   a.A = Ad; a.B = Bd; a.pA = pA; a.pB = pB; a.Lmax = Lmax;
   a.mtiles = (int)((M + BM - 1) / BM);

@@ -49,20 +49,55 @@ void rfm_prof_work(int fam, double units) {
   g_work[fam] += units;
 }
 
-void rfm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+namespace {
+thread_local bool t_count_paused = false;
+}  // namespace
+
+void rfm_count_pause(bool paused) { t_count_paused = paused; }
+void rfm_count_launch() {
+  if (!t_count_paused) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 void rfm_count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long rfm_launches_now() { return g_launches.load(std::memory_order_relaxed); }
 bool rfm_prof_active(unsigned int families) { return g_on && (g_mask & families) != 0; }
 
+// Per-device settings: the SM count and the dynamic shared-memory attributes
+// of kernels belong to one device's context, so they are cached per device
+// ordinal (a process may drive several GPUs from one library instance).
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+int g_sms[kMaxDevices];
+struct AttrSet {
+  int dev;
+  const void* func;
+  int bytes;
+};
+std::vector<AttrSet> g_attrs;
+}  // namespace
+
 int rfm_num_sms() {
-  static const int n = [] {  // initialised once, thread-safe
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return 0;
-    return v;
-  }();
-  return n;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (g_sms[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    g_sms[dev] = v;
+  }
+  return g_sms[dev];
+}
+
+cudaError_t rfm_smem_attr(const void* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  for (const AttrSet& a : g_attrs)
+    if (a.dev == dev && a.func == func && a.bytes >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) g_attrs.push_back({dev, func, bytes});
+  return e;
 }
 
 void* rfm_prof_begin(int fam, cudaStream_t st) {

@@ -419,8 +419,7 @@ QrScratch carve(double* scratch, long long n) {
 }
 
 rfm_status qr_init_device() {
-  static const cudaError_t attr = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       200 * 1024);  // once, thread-safe
+  const cudaError_t attr = rfm_smem_attr((const void*)k_panel, 200 * 1024);  // once per device
   if (attr != cudaSuccess || rfm_num_sms() == 0) {
     rfm_set_error("householder: device set-up failed");
     return RFM_ECUDA;
@@ -772,8 +771,7 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
     return RFM_EINVAL;
   }
   RFM_TRY(qr_init_device());
-  static const cudaError_t t_attr = cudaFuncSetAttribute(k_block_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)(QB * (QB + 1) * sizeof(double)));
+  const cudaError_t t_attr = rfm_smem_attr((const void*)k_block_t, (int)(QB * (QB + 1) * sizeof(double)));
   if (t_attr != cudaSuccess) {
     rfm_set_error("householder: k_block_t shared-memory attribute");
     return RFM_ECUDA;

@@ -112,9 +112,13 @@ void rfm_set_error(const std::string& msg);
   } while (0)
 void rfm_count_launch();
 void rfm_count_launches(long long k);  // kernels run by one replay of a captured graph
+void rfm_count_pause(bool paused);     // this thread's launches are being captured, not run
 long long rfm_launches_now();
 bool rfm_prof_active(unsigned int families);  // are any of these families (bit masks) being timed?
-int rfm_num_sms();  // SMs of the current device (0 if it cannot be queried)
+int rfm_num_sms();  // SMs of the current device (0 if it cannot be queried), cached per device
+// Sets a kernel's dynamic shared-memory limit once per (device, kernel); the
+// attribute belongs to the current device's context.
+cudaError_t rfm_smem_attr(const void* func, int bytes);
 #define RFM_CHECK_LAUNCH()                                                      \
   do {                                                                          \
     rfm_count_launch();                                                         \
@@ -188,6 +192,16 @@ rfm_status rfm_norm2(cudaStream_t st, const double* x, long long n, double* part
 rfm_status rfm_dot(cudaStream_t st, const double* x, const double* y, long long n, double* partial,
                    double* out_dev);
 
+#define RFM_SYNC_WORDS 4096
+// layout of p->sync
+#define SYNC_ERR 0
+#define SYNC_TICKET 8
+#define SYNC_EPOCH 9
+#define SYNC_LSQR_DONE 10
+#define SYNC_WAITLIM 11
+#define SYNC_BAR 16
+#define SYNC_FLAGS 64
+
 // ---- device helpers ------------------------------------------------------
 #ifdef __CUDACC__
 __device__ __forceinline__ double warp_sum(double v) {
@@ -210,13 +224,22 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
 }
 // Bounded wait until *flag == want.  Polls without sleeping first (a sleep's
 // granularity is far coarser than the expected wait), then backs off; gives up
-// after ~2^22 polls (well under a second of sleeping) and records the failure
-// in *err, so a missing producer never hangs the GPU.
+// after a poll limit and records the failure in *err, so a missing producer
+// never hangs the GPU.  `err` is word SYNC_ERR of a sync block whose word
+// SYNC_WAITLIM holds the limit: 0 the default of 2^22 polls (well under a
+// second of sleeping), a positive count that many polls, a negative value
+// "give up at once" (a host-side test setting, rfm_set_wait_limit).
 __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want,
                                           unsigned int* err) {
+  const int lim = (int)__ldcg(err + (SYNC_WAITLIM - SYNC_ERR));
+  if (lim < 0) {
+    atomicExch(err, 1u);
+    return false;
+  }
+  const unsigned int limit = lim == 0 ? (1u << 22) : (unsigned int)lim;
   unsigned int spins = 0;
   while (ld_acquire(flag) != want) {
-    if (++spins > (1u << 22)) {
+    if (++spins > limit) {
       atomicExch(err, 1u);
       return false;
     }
@@ -237,11 +260,4 @@ inline int rfm_swz128(int r, int k) {
   return (r >> 3) * 1024 + (r & 7) * 128 + (((chunk ^ (r & 7)) & 7) << 4) + ((k & 7) << 1);
 }
 
-#define RFM_SYNC_WORDS 4096
-// layout of p->sync
-#define SYNC_ERR 0
-#define SYNC_TICKET 8
-#define SYNC_EPOCH 9
-#define SYNC_LSQR_DONE 10
-#define SYNC_BAR 16
-#define SYNC_FLAGS 64
+

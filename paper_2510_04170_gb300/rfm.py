@@ -23,7 +23,7 @@ EXPORTS = ["rfm_default_opts", "rfm_last_error", "rfm_problem_create", "rfm_prob
            "rfm_feature_gram", "rfm_function_basis", "rfm_basis_combine", "rfm_warmstart_create",
            "rfm_warmstart_destroy", "rfm_warmstart_rank", "rfm_warmstart_network", "rfm_warmstart_train",
            "rfm_warmstart_predict", "rfm_batch_create", "rfm_batch_destroy", "rfm_batch_size", "rfm_batch_problem",
-           "rfm_batch_solve", "rfm_autotune_qr"]
+           "rfm_batch_solve", "rfm_autotune_qr", "rfm_set_wait_limit"]
 
 
 class RfmError(RuntimeError):
@@ -75,7 +75,8 @@ def load(path=LIB_PATH):
         "rfm_last_error": (ctypes.c_char_p, []),
         "rfm_problem_create": (I, [ctypes.POINTER(ProblemDesc), VP, ctypes.POINTER(P)]),
         "rfm_problem_destroy": (I, [P]),
-        "rfm_problem_sizes": (I, [P] + [ctypes.POINTER(I64)] * 6),
+        "rfm_problem_sizes": (I, [P] + [ctypes.POINTER(I64)] * 7),
+        "rfm_set_wait_limit": (I, [P, I64]),
         "rfm_get_features": (I, [P, VP]),
         "rfm_get_points": (I, [P, VP]),
         "rfm_assemble": (I, [P, VP, D, VP, VP]),
@@ -186,9 +187,9 @@ class Problem:
         self.stream = stream
         self._h = ctypes.c_void_p()
         _check(lib.rfm_problem_create(ctypes.byref(make_desc(desc)), _stream(stream), ctypes.byref(self._h)))
-        v = [ctypes.c_int64() for _ in range(6)]
+        v = [ctypes.c_int64() for _ in range(7)]
         _check(lib.rfm_problem_sizes(self._h, *[ctypes.byref(x) for x in v]))
-        self.m, self.n, self.W, self.G, self.m_int, self.m_iface = (x.value for x in v)
+        self.m, self.n, self.W, self.G, self.m_int, self.m_iface, self.nnz = (x.value for x in v)
 
     def close(self):
         if self._h:
@@ -238,6 +239,9 @@ class Problem:
     def rfm_set_precision(self, precision):
         _check(load().rfm_set_precision(self._h, precision))
 
+    def rfm_set_wait_limit(self, polls):
+        _check(load().rfm_set_wait_limit(self._h, polls))
+
     def rfm_sketch(self, kind, s, kJ, copy_out=True):
         B = self._dev(self.n, s) if copy_out else None
         _check(load().rfm_sketch(self._h, SKETCH[kind], s, kJ, _ptr(B)))
@@ -279,7 +283,9 @@ class Problem:
         c = torch.zeros(self.n, dtype=torch.float64, device="cuda") if c0 is None else c0.clone()
         info = SolveInfo()
         st = fn(self._h, ctypes.byref(make_opts(opts)), _ptr(c), ctypes.byref(info))
-        _check(st, ok=(RFM_OK, RFM_ENOCONV))
+        # a solver failure (iteration cap, non-finite residual) still returns
+        # the last iterate; info["status"] carries it
+        _check(st, ok=(RFM_OK, RFM_ENOCONV, RFM_ENONFINITE))
         return c, info.as_dict()
 
     def rfm_ipn_solve(self, opts, c0=None):
@@ -446,9 +452,9 @@ class _BorrowedProblem(Problem):
         self.desc = desc
         self.stream = None
         self._h = ctypes.c_void_p(handle)
-        v = [ctypes.c_int64() for _ in range(6)]
+        v = [ctypes.c_int64() for _ in range(7)]
         _check(lib.rfm_problem_sizes(self._h, *[ctypes.byref(x) for x in v]))
-        self.m, self.n, self.W, self.G, self.m_int, self.m_iface = (x.value for x in v)
+        self.m, self.n, self.W, self.G, self.m_int, self.m_iface, self.nnz = (x.value for x in v)
 
     def close(self):
         self._h = ctypes.c_void_p()

@@ -16,6 +16,12 @@ those of the configurations C1-C5 below):
               u* = prod sin(pi x_d)
   pde_kind 3  same operator as kind 2 with source A prod sin(q pi x_d) and
               homogeneous Dirichlet data (no closed-form solution)
+  pde_kind 4  Lap u - 100 u + 10 cosh(u) = f on [0,1]^3, u* = (2 + |x|^2) prod sin(pi x_d)
+              (Sec. 6.2, nonlinear Helmholtz equation)
+  pde_kind 5  -div((1 + u^2) grad u) = f on [0,1]^3, u* = (x+y+z) sin(pi x) sin(pi y) cos(pi z)
+              (Sec. 3.2 benchmark)
+  pde_kind 6  -div((1 + |grad u|^2) grad u) = f on [0,1]^3,
+              u* = sin(x(1-x)) sin(y(1-y)) e^(z+1/2)  (Sec. 6.2, strongly nonlinear)
 """
 from __future__ import annotations
 
@@ -30,6 +36,8 @@ FEATURE_SEED = 20251004
 #   kind 1: [eps_u, eps_v, F, k]
 #   kind 2: [kappa]
 #   kind 3: [kappa, amplitude A, frequency q]
+#   kind 4: [coefficient of u (-100), coefficient of cosh u (10)]
+#   kinds 5, 6: none
 
 
 def problem(dim, nsub, M, q_int, q_bdy, q_iface, *, fields=1, lo=None, hi=None,
@@ -46,7 +54,8 @@ def problem(dim, nsub, M, q_int, q_bdy, q_iface, *, fields=1, lo=None, hi=None,
 
 
 def _default_params(kind):
-    return {0: [1.0], 1: [2e-3, 1e-3, 0.04, 0.06], 2: [1.0], 3: [1.0, 1.0, 1.0]}[kind]
+    return {0: [1.0], 1: [2e-3, 1e-3, 0.04, 0.06], 2: [1.0], 3: [1.0, 1.0, 1.0], 4: [-100.0, 10.0],
+            5: [], 6: []}[kind]
 
 
 def solve_opts(**kw):
@@ -82,6 +91,20 @@ def config_c3():
     """3D steady Gray-Scott, two fields, 4x4x4 subdomains, M=256 per field."""
     return problem(3, (4, 4, 4), 256, (12, 12, 12), (6, 6, 6), (6, 6, 6),
                    fields=2, pde_kind=1)
+
+
+def grayscott_small():
+    """The Gray-Scott system of config_c3 at 2x2x2 subdomains and M=64 per
+    field (n=1,024), small enough for whole oracle solves."""
+    return problem(3, (2, 2, 2), 64, (12, 12, 12), (6, 6, 6), (6, 6, 6),
+                   fields=2, pde_kind=1)
+
+
+def paper_3d(kind, M, q=20):
+    """The 3D examples of Sec. 6.2 (and the Sec. 3.2 benchmark) at the paper's
+    settings: 2x2x2 subdomains, q^3 interior points and q x q points per face,
+    M features per subdomain (the paper's J)."""
+    return problem(3, (2, 2, 2), M, (q, q, q), (q, q, q), (q, q, q), pde_kind=kind)
 
 
 def config_c5(kappa=1.0, amp=1.0, freq=1.0):
