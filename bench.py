@@ -41,6 +41,8 @@ sys.path.insert(0, ROOT)
 
 import rfm_workloads as W  # noqa: E402
 
+T_START = time.time()
+
 METRIC = "Newton solves/s at rel-L2<=1e-6 vs FP64 oracle (IPN)"
 FP64_ALU_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 
@@ -57,6 +59,8 @@ def workload(name, precision=None, solver=None):
     elif name == "c2":
         p = 2 if precision is None else precision
         wl = dict(desc=W.config_c2(), opts=W.opts_c2(precision=p), solver=solver or "ipn", large=True,
+                  oracle_npz="c2_ipn_oracle.npz" if (solver or "ipn") == "ipn" else None, forms=True,
+                  oracle_timing="c2_oracle_timing.json",
                   label="c2: 3D -Lap u+u^3, 4x4x4 subdomains, M=512, n=32768, m=124416, Gaussian sketch s=65536")
     elif name == "c3":
         p = 2 if precision is None else precision
@@ -471,12 +475,28 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
 
-    # accuracy of the last solve
+    # accuracy of the last solve: against the manufactured solution and, where
+    # a stored whole oracle solve of this instance exists, against the oracle
     X = W.eval_grid(desc)
     u = gp.rfm_eval(c, torch.as_tensor(X, device="cuda")).cpu().numpy()
     from oracle.problem import Problem as OProblem  # exact solution formula only
     ue = OProblem(desc).exact(X)
-    rel_exact = float(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+    acc = {"status": STATUS[info["status"]], "final_resid": info["final_resid"],
+           "rel_l2_vs_exact": float(np.linalg.norm(u - ue) / np.linalg.norm(ue)),
+           "outer_iters": info["outer_iters"], "n_jac": info["n_jac"], "lsqr_iters_total": info["lsqr_iters_total"]}
+    ref = stored_oracle_solve(args, wl)
+    gate_ok = info["status"] == 0
+    if ref is not None:
+        rel_o = float(np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"]))
+        same = (info["outer_iters"] == int(ref["outer_iters"]) and info["n_jac"] == int(ref["n_jac"])
+                and info["lsqr_iters_total"] == int(np.sum(ref["lsqr_iters"])))
+        acc.update({"rel_l2_vs_oracle": rel_o, "oracle_counts": {
+            "outer_iters": int(ref["outer_iters"]), "n_jac": int(ref["n_jac"]),
+            "lsqr_iters_total": int(np.sum(ref["lsqr_iters"]))}, "counts_equal_oracle": same})
+        gate_ok = gate_ok and rel_o <= GATE_REL_L2
+    acc["gate"] = {"requires": f"status OK and rel-L2 vs the stored FP64 oracle solve <= {GATE_REL_L2:g}"
+                               if ref is not None else "status OK (no stored oracle solve of this instance)",
+                   "passed": bool(gate_ok)}
 
     # end to end through the public API from host memory
     e2e_times = []
@@ -499,14 +519,14 @@ def run_ours(args, rank, world, local_rank):
     steps_per_rank = args.steps
     roof = roofline(dom_fams, dom_ms, dom_cnt, dom_work)
     line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value if gate_ok else None, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * max_s / steps_per_rank, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["label"], "solver": wl["solver"], "parallelism": "replicas" if world > 1 else "1gpu",
                    "precision": PRECISION_NAMES[wl["precision"]],
                    "l2": "flushed (512 MiB write) between timed steps"},
-        "accuracy": {"rel_l2_vs_exact": rel_exact, "outer_iters": info["outer_iters"], "n_jac": info["n_jac"],
-                     "lsqr_iters_total": info["lsqr_iters_total"]},
+        "accuracy": acc,
         "phase_ms": {k: info[k] for k in ("t_assemble", "t_sketch", "t_qr", "t_lsqr", "t_linesearch", "t_total")},
         "kernel_ms_warmup_step": {k: round(v, 3) for k, v in fam_ms.items() if v > 0},
         "roofline": roof,
@@ -515,6 +535,10 @@ def run_ours(args, rank, world, local_rank):
                 "includes": "problem creation + H2D c0 + solve + D2H c"},
         "clocks": clk.summary(),
     }
+    if not gate_ok:
+        line["value_ungated"] = value
+    if wl.get("forms") and args.forms != "off" and world == 1:
+        line["forms"] = forms_record(args, wl, rfm, line, info)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget, info=info)
     if dist:
@@ -523,93 +547,164 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
+STATUS = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ERANK", "ENONFINITE", "ETIMEOUT"]
+GATE_REL_L2 = 1e-6
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_oracle_solve(args, wl):
+    """The stored whole oracle solve of this workload's instance (written by
+    tests/golden/make_c2_ipn_oracle.py, which calls only the oracle), or None."""
+    name = wl.get("oracle_npz")
+    if not name or not os.path.exists(os.path.join(GOLDEN, name)):
+        return None
+    return np.load(os.path.join(GOLDEN, name))
+
+
+def forms_record(args, wl, rfm, line, info):
+    """The metric's comparison on this GPU: plain FP64 IPN against each form
+    (mixed precision, batching, learned warm start).  Each entry is two timed
+    runs of the same instances that differ only in the option named, with the
+    accuracy of both.  The plain FP64 solve of the headline instance runs only
+    if the run stays within the wall-clock budget (--budget seconds since the
+    start); its projected duration is recorded either way."""
+    import torch
+    from paper_2510_04170_gb300 import warmstart
+    out = {}
+    # -- batching: the same instances on one stream vs eight (tensor-core QR)
+    descs = [d for i, d in enumerate(W.config_c4_instances(64, seed=1)) if i % 3 != 2][:args.forms_instances]
+    res = {}
+    for streams in (1, 8):
+        b = rfm.Batch(descs, streams=streams)
+        b.solve(W.solve_opts(precision=2, max_outer=1))  # graphs, buffers, first-touch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cs, infos, _ = b.solve(W.solve_opts(precision=2))
+        torch.cuda.synchronize()
+        res[streams] = (len(descs) / (time.perf_counter() - t0), cs, infos, b)
+    dev = max(float(torch.linalg.norm(a - z) / torch.linalg.norm(z)) for a, z in zip(res[8][1], res[1][1]))
+    out["batching"] = {"instances": f"{len(descs)} C4 instances with 2 or 3 subdomains per axis, M = 128/256",
+                       "single_stream_solves_per_s": res[1][0], "batched_8_streams_solves_per_s": res[8][0],
+                       "gain": res[8][0] / res[1][0], "max_rel_diff_c_batched_vs_single": dev}
+    for r in res.values():
+        r[3].close()
+    # -- learned warm start: zero start vs the network's prediction
+    ptrain = warmstart.sample_params(args.forms_train, 1)
+    ptest = warmstart.sample_params(args.forms_instances, 10001)
+    bt = rfm.Batch([warmstart.family_desc(p) for p in ptrain], streams=8)
+    ctrain, _, _ = bt.solve(W.solve_opts(precision=2))
+    bt.close()
+    ws = warmstart.train_warm_start(ptrain, torch.stack(ctrain), warmstart.family_desc(ptrain[0]))
+    del ctrain
+    bz = rfm.Batch([warmstart.family_desc(p) for p in ptest], streams=8)
+    params = torch.as_tensor(ptest, device="cuda")
+    bz.solve(W.solve_opts(precision=2, max_outer=1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cz, iz, _ = bz.solve(W.solve_opts(precision=2))
+    torch.cuda.synchronize()
+    tz = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c0 = ws.predict(params)
+    cw, iw, _ = bz.solve(W.solve_opts(precision=2), c0=[c0[i] for i in range(len(ptest))])
+    torch.cuda.synchronize()
+    tw = time.perf_counter() - t0
+    rel = []
+    for d, gp, a, z in zip(bz.descs, bz.problems, cw, cz):
+        Xe = torch.as_tensor(W.eval_grid(d, per_axis=4), device="cuda")
+        ua, uz = gp.rfm_eval(a, Xe), gp.rfm_eval(z, Xe)
+        rel.append(float(torch.linalg.norm(ua - uz) / torch.linalg.norm(uz)))
+    out["learned_warm_start"] = {
+        "instances": f"{len(ptest)} held-out instances of the C5 family (n = 4,096), network trained on "
+                     f"{len(ptrain)} solver outputs", "zero_start_solves_per_s": len(ptest) / tz,
+        "warm_start_solves_per_s": len(ptest) / tw, "gain": tz / tw, "prediction_included": True,
+        "n_jac_mean_zero": float(np.mean([i["n_jac"] for i in iz])),
+        "n_jac_mean_warm": float(np.mean([i["n_jac"] for i in iw])),
+        "rel_l2_warm_vs_zero_max": max(rel)}
+    bz.close()
+    # -- mixed precision: the headline instance in plain FP64
+    ph = info
+    est = (8.5 * ph["t_qr"] + 3.0 * ph["t_sketch"] + (ph["t_total"] - ph["t_qr"] - ph["t_sketch"])) / 1e3
+    elapsed = time.time() - T_START
+    mixed = {"solves_per_s": line["value"] if line["value"] is not None else line.get("value_ungated"),
+             "rel_l2_vs_oracle": line["accuracy"].get("rel_l2_vs_oracle")}
+    rec = {"mixed_solves_per_s": mixed["solves_per_s"], "mixed_rel_l2_vs_oracle": mixed["rel_l2_vs_oracle"],
+           "plain_projected_s": est}
+    if args.forms == "on" or elapsed + est <= args.budget:
+        import torch as _t
+        stream = _t.cuda.Stream()
+        with _t.cuda.stream(stream):
+            gp = rfm.Problem(wl["desc"], stream=stream)
+        opts0 = dict(wl["opts"], precision=0)
+        a = _t.cuda.Event(enable_timing=True)
+        b = _t.cuda.Event(enable_timing=True)
+        with _t.cuda.stream(stream):
+            a.record(stream)
+            c, inf0 = gp.rfm_ipn_solve(opts0)
+            b.record(stream)
+        b.synchronize()
+        t_plain = a.elapsed_time(b) / 1e3
+        X = W.eval_grid(wl["desc"])
+        u = gp.rfm_eval(c, _t.as_tensor(X, device="cuda")).cpu().numpy()
+        ref = stored_oracle_solve(args, wl)
+        rec.update({"plain_solves_per_s": 1.0 / t_plain, "plain_status": STATUS[inf0["status"]],
+                    "plain_counts": [inf0["outer_iters"], inf0["n_jac"], inf0["lsqr_iters_total"]],
+                    "gain": mixed["solves_per_s"] * t_plain if mixed["solves_per_s"] else None})
+        if ref is not None:
+            rec["plain_rel_l2_vs_oracle"] = float(np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"]))
+        gp.close()
+    else:
+        rec["plain"] = (f"skipped: {elapsed:.0f} s elapsed + {est:.0f} s projected exceeds the "
+                        f"{args.budget:.0f} s budget")
+    out["mixed_precision"] = rec
+    return out
+
+
 # ------------------------------------------------------------------ oracle
 def _threads():
-    try:
-        from threadpoolctl import threadpool_info
-        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        return os.cpu_count()
+    from oracle import timing
+    return timing.threads()
 
 
 def oracle_projection(wl, outer_iters, lsqr_iters, qr_cols=4096):
-    """Projected time of one oracle solve of a workload too large to run whole:
-    each oracle step is timed on a sample at the workload's sizes and scaled
-    by its operation count (assembly per row, Gaussian sketch per column
-    block, Householder QR per flop 2 n^2 (s - n/3), triangular solve per n^2,
-    block products per nonzero), with the iteration counts of the solve.
-    Returns (seconds per solve, sample description, seconds spent sampling)."""
-    import numpy as np
-    from oracle import assemble as asm
-    from oracle import linalg as la
-    from oracle import philox
-    from oracle.problem import Problem as OProblem
-    t_all = time.perf_counter()
-    desc, opts = wl["desc"], wl["opts"]
-    op = OProblem(desc)
-    n, m, W_ = op.n, op.m, op.W
-    s = opts["sketch_rows"] or int(math.ceil(opts["gamma"] * n))
-    c = np.zeros(n)
-    rng = np.random.default_rng(0)
-    # assembly of F and J: 2048 sampled rows
-    rows = np.sort(rng.choice(m, 2048, replace=False))
-    t0 = time.perf_counter()
-    asm.assemble_rows(op, c, rows)
-    t_asm = (time.perf_counter() - t0) * m / rows.size
-    if opts.get("sketch_kind", "count") == "gauss":
-        # Gaussian sketch of one column block (generation + product), times G blocks
-        blk_rows = np.nonzero((op.re0 == 0) | (op.re1 == 0))[0]
-        Jb = rng.standard_normal((blk_rows.size, W_))
-        t0 = time.perf_counter()
-        S = philox.gaussian_sketch(s, blk_rows, 0, desc["seed"])
-        S @ Jb
-        t_sk = (time.perf_counter() - t0) * op.G
-        del S
-    else:
-        # count sketch: the oracle adds dense rows of J; 2048 rows x 1024 columns, scaled to m x n
-        Jc = rng.standard_normal((2048, 1024))
-        t0 = time.perf_counter()
-        la.count_sketch(Jc, 4096, 0, desc["seed"])
-        t_sk = (time.perf_counter() - t0) * (m / 2048) * (n / 1024)
-    # Householder QR = per-column panel work (one s x 64 panel factorised)
-    # plus the blocked trailing update, 2 n^2 (s - n/3) flops at the rate of
-    # the oracle's own trailing-update products (V^T A, A -= V W) measured on
-    # an s x 64 by s x qr_cols sample
-    B = rng.standard_normal((s, 64))
-    t0 = time.perf_counter()
-    la.qr_r_blocked(B, nb=64)
-    t_col = (time.perf_counter() - t0) / 64
-    V = rng.standard_normal((s, 64))
-    A = rng.standard_normal((s, qr_cols))
-    t0 = time.perf_counter()
-    Wm = V.T @ A
-    A -= V @ Wm
-    rate = 4.0 * s * 64 * qr_cols / (time.perf_counter() - t0)
-    del B, V, A, Wm
-    t_qr = n * t_col + 2.0 * n * n * (s - n / 3.0) / rate
-    # triangular solve (n^2) and block product J x (nnz) per LSQR iteration
-    nt = 8192
-    Rs = np.triu(rng.standard_normal((nt, nt))) + nt * np.eye(nt)
-    t0 = time.perf_counter()
-    la.solve_upper(Rs, rng.standard_normal(nt))
-    t_tr = (time.perf_counter() - t0) * (n / nt) ** 2
-    Jr = rng.standard_normal((4096, W_))
-    xr = rng.standard_normal(W_)
-    t0 = time.perf_counter()
-    for _ in range(4):
-        Jr @ xr
-    t_mv = (time.perf_counter() - t0) / 4 * (m + op.m_iface) / 4096
-    t_it = 2 * t_tr + 2 * t_mv
-    # line search: about 19 residual evaluations per Newton step, each ~ an assembly
-    t_ls = 19 * t_asm * 0.5
-    per_solve = outer_iters * (t_asm + t_sk + t_qr + t_ls) + lsqr_iters * t_it
-    sk = (f"Gaussian sketch of 1 of {op.G} column blocks" if opts.get("sketch_kind", "count") == "gauss"
-          else "count sketch of 2048 x 1024")
-    sample = (f"oracle steps timed on samples and scaled by operation counts: assembly of 2048 rows, "
-              f"{sk}, Householder panel {s}x64 and "
-              f"trailing-update product {s}x64 by {s}x{qr_cols}, R solve n=8192, 4096-row block product; {outer_iters} outer and "
-              f"{lsqr_iters} LSQR iterations")
-    return per_solve, sample, time.perf_counter() - t_all
+    """The oracle's timing model (oracle.timing.projection) for a workload."""
+    from oracle import timing
+    return timing.projection(wl["desc"], wl["opts"], outer_iters, lsqr_iters, qr_cols)
+
+
+def oracle_counts(wl, info=None):
+    """Outer and LSQR iterations of the oracle's own solve of this instance
+    (stored whole solve), else those of the GPU solve."""
+    ref = stored_oracle_solve(None, wl)
+    if ref is not None:
+        return int(ref["outer_iters"]), int(np.sum(ref["lsqr_iters"])), "the stored oracle solve"
+    if info is not None:
+        return info["outer_iters"], info["lsqr_iters_total"], "the GPU solve"
+    return 4, 137, "assumed"
+
+
+def calibration(wl):
+    """measured / projected seconds of one whole oracle solve of this
+    instance on the machine that measured it (tests/golden/c2_oracle_timing.json,
+    written by tests/golden/calibrate_c2_oracle_model.py), or None."""
+    name = wl.get("oracle_timing")
+    path = os.path.join(GOLDEN, name) if name else None
+    if not path or not os.path.exists(path):
+        return None
+    return json.load(open(path))
+
+
+def projected_baseline(wl, info=None, qr_cols=4096):
+    """Oracle seconds per solve from its timing model on this host, scaled by
+    the model's calibration against a whole measured oracle solve."""
+    it, ls, src = oracle_counts(wl, info)
+    per, sample, t_sample = oracle_projection(wl, it, ls, qr_cols=qr_cols)
+    cal = calibration(wl)
+    factor = cal["measured_wall_s"] / cal["projected_s"] if cal else 1.0
+    extra = {"projected_seconds_per_solve": per, "counts_from": src}
+    if cal:
+        extra["calibration"] = {"factor": factor, **cal}
+    return per * factor, sample, t_sample, extra
 
 
 def cpu_baseline(wl, budget_s=15.0, info=None):
@@ -618,9 +713,9 @@ def cpu_baseline(wl, budget_s=15.0, info=None):
     from oracle.problem import Problem as OProblem
     desc, opts = wl["desc"], wl["opts"]
     if wl.get("large"):
-        per, sample, _ = oracle_projection(wl, info["outer_iters"], info["lsqr_iters_total"])
+        per, sample, _, extra = projected_baseline(wl, info)
         return {"value": 1.0 / per, "unit": "solves/s", "cores": _threads(), "kind": "oracle", "sample": sample,
-                "projected_seconds_per_solve": per}
+                **extra}
     op = OProblem(desc)
     t0 = time.perf_counter()
     count = 0
@@ -658,16 +753,19 @@ def run_reference(args, rank, world):
         el = sum(per)
         sample = "per step: " + cb["sample"]
     elif wl.get("large"):
-        # each step: one bounded sample of the oracle's steps, projected to a solve
-        # (iteration counts of the GPU solve of this workload: IT 4, 137 LSQR steps)
-        per = []
+        # each step: one bounded sample of the oracle's steps (the same model as
+        # the cpu_baseline leg of the GPU arm), projected to a solve; the step
+        # lasts as long as its sample, so a step is that fraction of a solve
+        per, spent = [], []
         for i in range(args.warmup + args.steps):
-            p_, sample, _ = oracle_projection(wl, 4, 137, qr_cols=2048)
+            p_, sample, t_s, extra = projected_baseline(wl)
             if i >= args.warmup:
                 per.append(p_)
+                spent.append(t_s)
         v = 1.0 / statistics.median(per)
-        el = sum(per)
-        sample = "per step: " + sample
+        el = sum(spent)
+        sample = ("per step: " + sample + f"; each step is {statistics.median(spent) / statistics.median(per):.2e} "
+                  "of a solve")
     else:
         op = OProblem(wl["desc"])
         fn = getattr(newton, wl["solver"])
@@ -703,6 +801,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=None,
                     help="c4/c5: use only this many instances (functional runs; the label says so)")
+    ap.add_argument("--forms", default="auto", choices=["auto", "on", "off"],
+                    help="c2: add the plain-vs-forms comparison (auto: the plain FP64 solve only within --budget)")
+    ap.add_argument("--budget", type=float, default=1500.0, help="wall-clock seconds for --forms auto")
+    ap.add_argument("--forms-instances", type=int, default=16)
+    ap.add_argument("--forms-train", type=int, default=64)
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 2 if args.workload == "c2" else 10

@@ -49,7 +49,15 @@ typedef struct rfm_problem rfm_problem;
  * cont_order continuity orders C^0..C^{k-1} across interfaces.
  * pde_kind: 0 -Lap u + p0 u^3 = f; 1 Gray-Scott (2 fields: eps_u, eps_v, F, k);
  *           2 -div(a grad u) + p0 u^3 = f, a = 1 + 0.5 sin(2 pi x);
- *           3 kind 2 with source p1 prod sin(p2 pi x_d) and zero Dirichlet data. */
+ *           3 kind 2 with source p1 prod sin(p2 pi x_d) and zero Dirichlet data;
+ *           4 Lap u + p0 u + p1 cosh(u) = f (nonlinear Helmholtz, Sec. 6.2:
+ *             p0 = -100, p1 = 10), u* = (2 + |x|^2) prod sin(pi x_d);
+ *           5 -div((1 + u^2) grad u) = f (Sec. 3.2 benchmark),
+ *             u* = (x + y + z) sin(pi x) sin(pi y) cos(pi z);
+ *           6 -div((1 + |grad u|^2) grad u) = f (strongly nonlinear, Sec. 6.2),
+ *             u* = sin(x(1-x)) sin(y(1-y)) e^(z+1/2).
+ *           Kinds 4-6 are three-dimensional with one field; f and the Dirichlet
+ *           data g = u* come from the manufactured u*. */
 typedef struct {
   int dim;
   double lo[3], hi[3];
@@ -110,7 +118,8 @@ const char* rfm_last_error(void);
  * features (Philox, Sec. 2.2) and the collocation points and right-hand sides
  * (Sec. 5) on the device.  `cuda_stream` is a cudaStream_t or NULL.
  * Errors: RFM_EINVAL for dim not in {2,3}, non-positive counts, fields not 1
- * or 2, cont_order not in {1,2}; RFM_ENOMEM/RFM_ECUDA on device failures. */
+ * or 2, cont_order not in {1,2}, pde_kind outside 0..6 or its dimension and
+ * field count; RFM_ENOMEM/RFM_ECUDA on device failures. */
 rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, rfm_problem** out);
 rfm_status rfm_problem_destroy(rfm_problem* p);
 

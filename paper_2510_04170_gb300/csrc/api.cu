@@ -233,10 +233,15 @@ struct Timer {
 enum { WV_U, WV_V, WV_W, WV_X, WV_TN, WV_TN2, WV_TM, WV_D, WV_Z, WV_FPREV, WV_FNEW, WV_P0, WV_P1, WV_UU, WV_VV, WV_B,
        WV_COUNT };
 
-double* wv(rfm_problem* p, int slot) {
-  const long long stride = std::max(p->m * std::max(1, p->fields), p->n) + 64;
-  return p->work + (size_t)slot * stride;
+// Doubles per work-vector slot: an m-vector of per-row quantities (the
+// line-search split stores `fields` values per row, or the 10-entry 2-jet of
+// u for PDE kinds 4-6) or an n-vector.
+long long vec_stride(const rfm_problem* p) {
+  const long long per_row = p->desc.pde_kind >= 4 ? 10 : std::max(1, p->fields);
+  return std::max(p->m * per_row, p->n) + 64;
 }
+
+double* wv(rfm_problem* p, int slot) { return p->work + (size_t)slot * vec_stride(p); }
 
 rfm_status read_scalars(rfm_problem* p, const double* dev, int count, double* host) {
   RFM_CUDA(cudaMemcpyAsync(p->hostbuf, dev, count * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
@@ -766,8 +771,8 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
   const int D = desc->dim;
   if (D < 2 || D > 3 || desc->M <= 0 || desc->fields < 1 || desc->fields > RFM_MAX_FIELDS ||
       desc->cont_order < 1 || desc->cont_order > 2 || desc->fields * desc->M > RFM_MAX_WIDTH ||
-      desc->pde_kind < 0 || desc->pde_kind > 3 || (desc->pde_kind == 1 && (desc->fields != 2 || D != 3)) ||
-      (desc->pde_kind != 1 && desc->fields != 1)) {
+      desc->pde_kind < 0 || desc->pde_kind > 6 || (desc->pde_kind == 1 && (desc->fields != 2 || D != 3)) ||
+      (desc->pde_kind >= 4 && D != 3) || (desc->pde_kind != 1 && desc->fields != 1)) {
     g_err = "invalid problem description";
     return RFM_EINVAL;
   }
@@ -835,8 +840,7 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
     TRYA(dalloc(&p->hsign, p->m));
     TRYA(dalloc(&p->red, 4096));
     TRYA(dalloc(&p->sync, RFM_SYNC_WORDS));
-    const long long stride = std::max(p->m * std::max(1, p->fields), p->n) + 64;
-    p->work_cap = stride * WV_COUNT;
+    p->work_cap = vec_stride(p) * WV_COUNT;
     TRYA(dalloc(&p->work, p->work_cap));
     if (cudaMallocHost((void**)&p->hostbuf, 64 * sizeof(double)) != cudaSuccess) {
       g_err = "cudaMallocHost failed";

@@ -55,8 +55,119 @@ __device__ __forceinline__ double grid_pt(const double* X, int nbp, int b, int j
   return a + ((c - a) * (double)p) / (double)(q - 1);
 }
 
+// Value, gradient and Hessian (H00 H11 H22 H01 H02 H12) of the manufactured
+// solutions of the 3D examples of Sec. 6.2 (kinds 4-6), each a product of
+// one-variable factors differentiated by hand:
+//   kind 4  u = (2 + x^2 + y^2 + z^2) sin(pi x) sin(pi y) sin(pi z)
+//   kind 5  u = (x + y + z) sin(pi x) sin(pi y) cos(pi z)
+//   kind 6  u = sin(x(1-x)) sin(y(1-y)) e^(z + 1/2)
+__device__ void exact_jet3(int kind, const double* x, double& u, double* g, double* h) {
+  double f[3][3];  // factor b: value, first, second derivative
+  if (kind == 6) {
+    for (int b = 0; b < 2; ++b) {
+      const double w = x[b] * (1.0 - x[b]), sw = sin(w), cw = cos(w), dw = 1.0 - 2.0 * x[b];
+      f[b][0] = sw;
+      f[b][1] = cw * dw;
+      f[b][2] = -sw * dw * dw - 2.0 * cw;
+    }
+    const double e = exp(x[2] + 0.5);
+    f[2][0] = f[2][1] = f[2][2] = e;
+  } else {
+    for (int b = 0; b < 3; ++b) {
+      const double sn = sin(kPi * x[b]), cs = cos(kPi * x[b]);
+      if (kind == 5 && b == 2) {
+        f[b][0] = cs;
+        f[b][1] = -kPi * sn;
+        f[b][2] = -kPi * kPi * cs;
+      } else {
+        f[b][0] = sn;
+        f[b][1] = kPi * cs;
+        f[b][2] = -kPi * kPi * sn;
+      }
+    }
+  }
+  // P = f0 f1 f2 and its derivatives
+  const double P = f[0][0] * f[1][0] * f[2][0];
+  const double dP[3] = {f[0][1] * f[1][0] * f[2][0], f[0][0] * f[1][1] * f[2][0], f[0][0] * f[1][0] * f[2][1]};
+  const double hP[6] = {f[0][2] * f[1][0] * f[2][0], f[0][0] * f[1][2] * f[2][0], f[0][0] * f[1][0] * f[2][2],
+                        f[0][1] * f[1][1] * f[2][0], f[0][1] * f[1][0] * f[2][1], f[0][0] * f[1][1] * f[2][1]};
+  if (kind == 6) {
+    u = P;
+    for (int b = 0; b < 3; ++b) g[b] = dP[b];
+    for (int k = 0; k < 6; ++k) h[k] = hP[k];
+    return;
+  }
+  // u = r P with r = 2 + |x|^2 (kind 4) or x + y + z (kind 5)
+  double r, dr[3], hr;
+  if (kind == 4) {
+    r = 2.0 + x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    for (int b = 0; b < 3; ++b) dr[b] = 2.0 * x[b];
+    hr = 2.0;  // diagonal of Hess r; off-diagonal 0
+  } else {
+    r = x[0] + x[1] + x[2];
+    for (int b = 0; b < 3; ++b) dr[b] = 1.0;
+    hr = 0.0;
+  }
+  u = r * P;
+  for (int b = 0; b < 3; ++b) g[b] = dr[b] * P + r * dP[b];
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int k = 0; k < 6; ++k) {
+    const int a = ia[k], b = ib[k];
+    h[k] = (k < 3 ? hr * P : 0.0) + dr[a] * dP[b] + dP[a] * dr[b] + r * hP[k];
+  }
+}
+
+// Residual of an interior row of kinds 4-6 from the 2-jet Q = (u, grad u,
+// Hess u as H00 H11 H22 H01 H02 H12) of the solution at the point, and its
+// partial derivatives C = dR/dQ (the Jacobian row is then
+// sum_k C_k (2-jet of phi_j)_k):
+//   kind 4  R = Lap u + p0 u + p1 cosh(u)                       (Sec. 6.2, Helmholtz)
+//   kind 5  R = -(1 + u^2) Lap u - 2 u |grad u|^2               (-div((1 + u^2) grad u))
+//   kind 6  R = -(1 + |g|^2) Lap u - 2 g^T H g                  (-div((1 + |grad u|^2) grad u))
+__device__ __forceinline__ double jet_residual(const PdeConst& pc, const double* Q, double* C) {
+  const double u = Q[0], g0 = Q[1], g1 = Q[2], g2 = Q[3];
+  const double H00 = Q[4], H11 = Q[5], H22 = Q[6], H01 = Q[7], H02 = Q[8], H12 = Q[9];
+  const double lap = H00 + H11 + H22;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) C[k] = 0.0;
+  if (pc.kind == 4) {
+    C[0] = pc.p[0] + pc.p[1] * sinh(u);
+    C[4] = C[5] = C[6] = 1.0;
+    return lap + pc.p[0] * u + pc.p[1] * cosh(u);
+  }
+  const double gg = g0 * g0 + g1 * g1 + g2 * g2;
+  if (pc.kind == 5) {
+    const double L = 1.0 + u * u;
+    C[0] = -2.0 * u * lap - 2.0 * gg;
+    C[1] = -4.0 * u * g0;
+    C[2] = -4.0 * u * g1;
+    C[3] = -4.0 * u * g2;
+    C[4] = C[5] = C[6] = -L;
+    return -L * lap - 2.0 * u * gg;
+  }
+  const double L = 1.0 + gg;
+  const double Hg0 = H00 * g0 + H01 * g1 + H02 * g2;
+  const double Hg1 = H01 * g0 + H11 * g1 + H12 * g2;
+  const double Hg2 = H02 * g0 + H12 * g1 + H22 * g2;
+  C[1] = -2.0 * g0 * lap - 4.0 * Hg0;
+  C[2] = -2.0 * g1 * lap - 4.0 * Hg1;
+  C[3] = -2.0 * g2 * lap - 4.0 * Hg2;
+  C[4] = -L - 2.0 * g0 * g0;
+  C[5] = -L - 2.0 * g1 * g1;
+  C[6] = -L - 2.0 * g2 * g2;
+  C[7] = -4.0 * g0 * g1;
+  C[8] = -4.0 * g0 * g2;
+  C[9] = -4.0 * g1 * g2;
+  return -L * lap - 2.0 * (g0 * Hg0 + g1 * Hg1 + g2 * Hg2);
+}
+
 __device__ double exact_field(const PdeConst& pc, const double* x, int f) {
   if (pc.kind == 3) return 0.0;
+  if (pc.kind >= 4) {
+    double u, g[3], h[6];
+    exact_jet3(pc.kind, x, u, g, h);
+    return u;
+  }
   if (pc.kind == 1 && f == 0) {
     const double ax = x[0] * (1.0 - x[0]), ay = x[1] * (1.0 - x[1]);
     return sin(ax) * sin(ay) * exp(x[2]);
@@ -85,6 +196,11 @@ __device__ double source_term(const PdeConst& pc, const double* x, int f) {
     double s = 1.0;
     for (int b = 0; b < d; ++b) s = s * sin(pc.p[2] * pi * x[b]);
     return pc.p[1] * s;
+  }
+  if (pc.kind >= 4) {
+    double Q[10], C[10];
+    exact_jet3(pc.kind, x, Q[0], Q + 1, Q + 4);
+    return jet_residual(pc, Q, C);
   }
   // kind 1: Gray-Scott with u = sin(x(1-x)) sin(y(1-y)) e^z, v = prod sin(pi x_b)
   const double eu = pc.p[0], ev = pc.p[1], Fc = pc.p[2], kk = pc.p[3];
@@ -242,7 +358,72 @@ __global__ void __launch_bounds__(128) k_assemble(PdeConst pc, const double* __r
     const double x[3] = {xp.x, xp.y, xp.z};
     double Fi = 0.0, Fd = 0.0;
     double rowmax = 0.0;
-    if (kind == 0) {
+    if (kind == 0 && pc.kind >= 4) {
+      // kinds 4-6 (one field, 3D): the residual is a function of the 2-jet
+      // of u at the point.  Pass 1 accumulates the jet, the residual gives
+      // the coefficients C = dR/dQ, pass 2 forms J_j = sum_k C_k jet_k(phi_j).
+      const RowGeo g = row_geo(mu, sig, e0, x, d);
+      const long long fb = (long long)e0 * M;
+      double Q[10], Qd[10];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        Q[k] = 0.0;
+        Qd[k] = 0.0;
+      }
+      for (int j = lane; j < M; j += 32) {
+        const double4 kb = *reinterpret_cast<const double4*>(feat + 4 * (fb + j));
+        double t, s1;
+        feature_at(kb, g, d, t, s1);
+        const double k0 = kb.x / g.sg[0], k1 = kb.y / g.sg[1], k2 = kb.z / g.sg[2];
+        const double h = -2.0 * t * s1;
+        const double jt[10] = {t, s1 * k0, s1 * k1, s1 * k2, h * k0 * k0, h * k1 * k1, h * k2 * k2,
+                               h * k0 * k1, h * k0 * k2, h * k1 * k2};
+        const double cj = c[fb + j];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) Q[k] += cj * jt[k];
+        if (MODE == MODE_LS) {
+          const double dj = dv[fb + j];
+#pragma unroll
+          for (int k = 0; k < 10; ++k) Qd[k] += dj * jt[k];
+        }
+        if (MODE == MODE_JF) {
+          sA[j] = t;
+          sB[j] = s1;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        Q[k] = warp_sum(Q[k]);
+        if (MODE == MODE_LS) Qd[k] = warp_sum(Qd[k]);
+      }
+      if (MODE == MODE_LS) {
+        if (lane == 0) {
+          Fout[i] = -rhs[i];
+          P1[i] = 0.0;
+#pragma unroll
+          for (int k = 0; k < 10; ++k) {
+            U[i * 10 + k] = Q[k];
+            V[i * 10 + k] = Qd[k];
+          }
+        }
+        continue;
+      }
+      double C[10];
+      Fi = jet_residual(pc, Q, C) - rhs[i];
+      if (MODE == MODE_JF) {
+        __syncwarp();
+        for (int j = lane; j < M; j += 32) {
+          const double4 kb = *reinterpret_cast<const double4*>(feat + 4 * (fb + j));
+          const double k0 = kb.x / g.sg[0], k1 = kb.y / g.sg[1], k2 = kb.z / g.sg[2];
+          const double t = sA[j], s1 = sB[j], h = -2.0 * t * s1;
+          const double Jv = C[0] * t + s1 * (C[1] * k0 + C[2] * k1 + C[3] * k2) +
+                            h * (C[4] * k0 * k0 + C[5] * k1 * k1 + C[6] * k2 * k2 + C[7] * k0 * k1 +
+                                 C[8] * k0 * k2 + C[9] * k1 * k2);
+          sA[j] = Jv;
+          rowmax = fmax(rowmax, fabs(Jv));
+        }
+      }
+    } else if (kind == 0) {
       const RowGeo g = row_geo(mu, sig, e0, x, d);
       double a = 0.0, ax = 0.0;
       if (pc.kind >= 2) {
@@ -376,7 +557,12 @@ __global__ void k_ls_eval(PdeConst pc, const int4* __restrict__ meta, const doub
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
     double val = P0[i] + alpha * P1[i];
     const int kind = meta[i].x & 0xF;
-    if (kind == 0) {
+    if (kind == 0 && pc.kind >= 4) {
+      double q[10], C[10];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) q[k] = U[i * 10 + k] + alpha * V[i * 10 + k];
+      val += jet_residual(pc, q, C);
+    } else if (kind == 0) {
       const int f = (meta[i].x >> 4) & 0xF;
       double u[2] = {0, 0}, coef[2];
       for (int ff = 0; ff < pc.fields; ++ff) u[ff] = U[i * pc.fields + ff] + alpha * V[i * pc.fields + ff];

@@ -107,6 +107,12 @@ def paper_3d(kind, M, q=20):
     return problem(3, (2, 2, 2), M, (q, q, q), (q, q, q), (q, q, q), pde_kind=kind)
 
 
+def operator_small(kind):
+    """Kinds 4-6 at 2x2x2 subdomains, M = 100 (n = 800), 8^3 interior points
+    and 8 x 8 per face: whole oracle solves take under a minute."""
+    return problem(3, (2, 2, 2), 100, (8, 8, 8), (8, 8, 8), (8, 8, 8), pde_kind=kind)
+
+
 def config_c5(kappa=1.0, amp=1.0, freq=1.0):
     """Learned-warm-start family: 2x2x2 subdomains, M=512 (n=4,096)."""
     return problem(3, (2, 2, 2), 512, (12, 12, 12), (6, 6, 6), (6, 6, 6),

@@ -51,6 +51,9 @@ CASES = {
     "3d_kind2": W.small_3d(pde_kind=2, pde_params=[3.0]),
     "3d_kind3": W.small_3d(pde_kind=3, pde_params=[2.0, 1.5, 2.0]),
     "3d_grayscott": W.small_3d(pde_kind=1, fields=2, M=20),
+    "3d_helmholtz": W.small_3d(pde_kind=4, M=20),
+    "3d_quasilinear": W.small_3d(pde_kind=5, M=20),
+    "3d_strongly_nonlinear": W.small_3d(pde_kind=6, M=20),
 }
 
 
@@ -220,7 +223,8 @@ def test_lsqr_direction(name):
     assert np.linalg.norm(J @ (host(d) - do)) <= 1e-7 * np.linalg.norm(J @ do)
 
 
-@pytest.mark.parametrize("name", ["2d_c1", "3d_small", "3d_grayscott"])
+@pytest.mark.parametrize("name", ["2d_c1", "3d_small", "3d_grayscott", "3d_helmholtz", "3d_quasilinear",
+                                  "3d_strongly_nonlinear"])
 def test_linesearch(name):
     desc = CASES[name]
     op = OProblem(desc)
@@ -275,3 +279,7 @@ def test_invalid_descriptions_are_rejected():
     assert e.value.status == rfm.RFM_EINVAL
     with pytest.raises(rfm.RfmError):
         rfm.Problem(W.with_(W.small_3d(), fields=2))   # two fields only for Gray-Scott
+    with pytest.raises(rfm.RfmError):
+        rfm.Problem(W.small_2d(pde_kind=5))            # kinds 4-6 are three-dimensional
+    with pytest.raises(rfm.RfmError):
+        rfm.Problem(W.small_3d(pde_kind=7, pde_params=[0.0]))
