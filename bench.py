@@ -805,7 +805,7 @@ def main():
                     help="c2: add the plain-vs-forms comparison (auto: the plain FP64 solve only within --budget)")
     ap.add_argument("--budget", type=float, default=1500.0, help="wall-clock seconds for --forms auto")
     ap.add_argument("--forms-instances", type=int, default=16)
-    ap.add_argument("--forms-train", type=int, default=64)
+    ap.add_argument("--forms-train", type=int, default=128)
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 2 if args.workload == "c2" else 10

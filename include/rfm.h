@@ -56,8 +56,16 @@ typedef struct rfm_problem rfm_problem;
  *             u* = (x + y + z) sin(pi x) sin(pi y) cos(pi z);
  *           6 -div((1 + |grad u|^2) grad u) = f (strongly nonlinear, Sec. 6.2),
  *             u* = sin(x(1-x)) sin(y(1-y)) e^(z+1/2).
- *           Kinds 4-6 are three-dimensional with one field; f and the Dirichlet
- *           data g = u* come from the manufactured u*. */
+ *           7 -div((1 + u^2) grad u) + u^3 - u + e^u = f (diffusion-reaction on
+ *             the unit ball, Sec. 6.2), u* = |x|^2 prod sin(pi x_d).
+ *           Kinds 4-7 are three-dimensional with one field; f and the Dirichlet
+ *           data g = u* come from the manufactured u*.
+ * geometry 1 (the unit ball, Sec. 6.2): the box [lo, hi] is split into the
+ * subdomains as usual, interior and interface grid points with
+ * x^2 + y^2 + z^2 < 1 are kept, and the Dirichlet rows sit at n_sphere points
+ * of the unit sphere placed by the Fibonacci spiral (z_i = 1 - (2i+1)/N,
+ * azimuth i pi (3 - sqrt 5)), each in the subdomain that contains it; rows are
+ * interior, interface, then boundary points grouped by subdomain.  dim 3. */
 typedef struct {
   int dim;
   double lo[3], hi[3];
@@ -72,6 +80,8 @@ typedef struct {
   uint64_t seed;
   int pde_kind;
   double pde_params[8];
+  int geometry;       /* 0: the box [lo, hi]; 1: the unit ball inside it (below) */
+  int64_t n_sphere;   /* geometry 1: Dirichlet points on the unit sphere       */
 } rfm_problem_desc;
 
 enum { RFM_SKETCH_COUNT = 0, RFM_SKETCH_GAUSS = 1 };
@@ -118,8 +128,9 @@ const char* rfm_last_error(void);
  * features (Philox, Sec. 2.2) and the collocation points and right-hand sides
  * (Sec. 5) on the device.  `cuda_stream` is a cudaStream_t or NULL.
  * Errors: RFM_EINVAL for dim not in {2,3}, non-positive counts, fields not 1
- * or 2, cont_order not in {1,2}, pde_kind outside 0..6 or its dimension and
- * field count; RFM_ENOMEM/RFM_ECUDA on device failures. */
+ * or 2, cont_order not in {1,2}, pde_kind outside 0..7 or its dimension and
+ * field count, geometry outside 0..1 (1 needs dim 3 and n_sphere > 0);
+ * RFM_ENOMEM/RFM_ECUDA on device failures. */
 rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, rfm_problem** out);
 rfm_status rfm_problem_destroy(rfm_problem* p);
 

@@ -21,6 +21,7 @@ Operators (pde_kind):
   6  F = -div((1 + |grad u|^2) grad u) - f = -(1 + |g|^2) Lap u - 2 g^T H g - f
      J = -(1 + |g|^2) Lap phi - 2 Lap u (g . grad phi) - 4 grad phi . H g - 2 g^T Hess(phi) g
      (strongly nonlinear example of Sec. 6.2; g = grad u, H = Hess u)
+  7  kind 5 plus the reaction u^3 - u + e^u (unit-ball example of Sec. 6.2)
   2,3 F = -a Lap u - a_x u_x + kap u^3 - f    J = -a Lap phi - a_x phi_x + 3 kap u^2 phi
       with a = 1 + 0.5 sin(2 pi x), a_x = pi cos(2 pi x)
   1  (Gray-Scott, fields u, v)
@@ -137,7 +138,7 @@ def assemble_rows(prob, c, rows, want_jacobian=True):
                 Jv_v = -ev * lap[:, 1] + (-2.0 * uu * vv + (Fc + kk))[:, None] * phi[:, 1]
                 Jp[sel[t0], :M] = Ju_u[t0]; Jp[sel[t0], M:] = Ju_v[t0]
                 Jp[sel[t1], :M] = Jv_u[t1]; Jp[sel[t1], M:] = Jv_v[t1]
-        elif k in (4, 5, 6):
+        elif k in (4, 5, 6, 7):
             # 3D examples of Sec. 6.2 (one field), from the 2-jet of u at the point
             phi0, grad0, lap0 = phi[:, 0], grad[:, 0], lap[:, 0]
             cb0 = cb[:, 0]
@@ -150,13 +151,17 @@ def assemble_rows(prob, c, rows, want_jacobian=True):
                 F[sel] = lu0 + p[0] * uu + p[1] * np.cosh(uu) - src
                 if want_jacobian:
                     Jp[sel, :M] = lap0 + (p[0] + p[1] * np.sinh(uu))[:, None] * phi0
-            elif k == 5:
-                # -div((1 + u^2) grad u) = -(1 + u^2) Lap u - 2 u |grad u|^2
+            elif k in (5, 7):
+                # -div((1 + u^2) grad u) = -(1 + u^2) Lap u - 2 u |grad u|^2,
+                # kind 7 adds the reaction u^3 - u + e^u (unit-ball example)
                 F[sel] = -(1.0 + uu * uu) * lu0 - 2.0 * uu * gg - src
+                if k == 7:
+                    F[sel] += uu ** 3 - uu + np.exp(uu)
                 if want_jacobian:
                     gphi = np.einsum("rmb,rb->rm", grad0, gu)       # grad u . grad phi_j
+                    react = 3.0 * uu * uu - 1.0 + np.exp(uu) if k == 7 else 0.0 * uu
                     Jp[sel, :M] = (-(1.0 + uu * uu)[:, None] * lap0
-                                   - (2.0 * uu * lu0 + 2.0 * gg)[:, None] * phi0
+                                   - (2.0 * uu * lu0 + 2.0 * gg - react)[:, None] * phi0
                                    - (4.0 * uu)[:, None] * gphi)
             else:
                 # -div((1 + |grad u|^2) grad u) = -(1 + |g|^2) Lap u - 2 g^T H g

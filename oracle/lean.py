@@ -173,7 +173,9 @@ def qr_r_blocked_inplace(A, nb=64, chunk=2048):
             v, tau, beta = la.house(A[j:, j])
             if tau != 0.0 and j + 1 < j1:
                 w = v @ A[j:, j + 1:j1]
-                A[j:, j + 1:j1] -= tau * np.outer(v, w)
+                # tau * (v_r w_k) as in linalg.qr_r_blocked, formed column-major
+                # (np.outer(w, v).T) to match A's layout
+                A[j:, j + 1:j1] -= tau * np.outer(w, v).T
             A[j, j] = beta
             A[j + 1:, j] = 0.0
             V[jj:, jj] = v

@@ -25,6 +25,20 @@ import numpy as np
 from . import philox
 
 
+def fibonacci_sphere(count):
+    """`count` points spread uniformly over the unit sphere by the Fibonacci
+    (golden-angle) spiral: z_i = 1 - (2 i + 1) / count, radius sqrt(1 - z_i^2),
+    azimuth i * pi (3 - sqrt 5)."""
+    ga = math.pi * (3.0 - math.sqrt(5.0))
+    out = np.zeros((count, 3))
+    for i in range(count):
+        z = 1.0 - (2.0 * i + 1.0) / count
+        r = math.sqrt(1.0 - z * z)
+        th = i * ga
+        out[i] = (r * math.cos(th), r * math.sin(th), z)
+    return out
+
+
 class Problem:
     def __init__(self, desc):
         self.desc = desc
@@ -95,11 +109,15 @@ class Problem:
             axis.append(np.full(r, ax)); sord.append(np.full(r, s)); field.append(np.full(r, f))
             side.append(np.full(r, sd)); pts.append(P)
 
+        ball = desc.get("geometry", "box") == "ball"
+        # inside the ball: (x^2 + y^2) + z^2 < 1, summed in that order
+        keep = (lambda P: P[(P[:, 0] * P[:, 0] + P[:, 1] * P[:, 1]) + P[:, 2] * P[:, 2] < 1.0]) if ball \
+            else (lambda P: P)
         qi = desc["q_int"]
         for e in range(self.G):
             axes = [self.grid1d(b, self.idx[e][b], qi[b]) for b in range(d)]
             mesh = np.meshgrid(*axes, indexing="ij")
-            P = np.stack([m.reshape(-1) for m in mesh], axis=1)
+            P = keep(np.stack([m.reshape(-1) for m in mesh], axis=1))
             for f in range(self.fields):
                 add(P, 0, e, -1, -1, 0, f, -1)
         self.m_int = sum(p.shape[0] for p in pts)
@@ -112,11 +130,25 @@ class Problem:
                 e2 = self.sub_id(nb)
                 P = self._face_points(e, a, desc["q_iface"])
                 P[:, a] = self.X[a][idx[a] + 1]
+                P = keep(P)
                 for f in range(self.fields):
                     for s in range(self.cont):
                         add(P, 1, e, e2, a, s, f, -1)
         self.m_iface = sum(p.shape[0] for p in pts) - self.m_int
-        for a in range(d):
+        if ball:
+            # Dirichlet rows at Fibonacci points of the unit sphere, grouped by
+            # the subdomain that contains them (Sec. 6.2, unit-ball example)
+            F = fibonacci_sphere(int(desc["n_sphere"]))
+            own = np.zeros(F.shape[0], dtype=np.int64)
+            for b in range(d):
+                t = np.floor((F[:, b] - self.lo[b]) / (self.hi[b] - self.lo[b]) * self.N[b]).astype(np.int64)
+                own = own * self.N[b] + np.clip(t, 0, self.N[b] - 1)
+            for e in range(self.G):
+                sel = np.nonzero(own == e)[0]
+                if sel.size:
+                    for f in range(self.fields):
+                        add(F[sel], 2, e, -1, -1, 0, f, -1)
+        for a in range(d if not ball else 0):
             for sd in (0, 1):
                 for e in range(self.G):
                     if self.idx[e][a] != (0 if sd == 0 else self.N[a] - 1):
@@ -146,7 +178,7 @@ class Problem:
             x, y, z = X[:, 0], X[:, 1], X[:, 2]
             u = np.sin(x * (1 - x)) * np.sin(y * (1 - y)) * np.exp(z)
             return np.stack([u, S], axis=1)
-        if k in (4, 5, 6):
+        if k in (4, 5, 6, 7):
             return self.exact_jet(X)[0][:, None]
         return np.full((X.shape[0], 1), np.nan)
 
@@ -156,6 +188,7 @@ class Problem:
           kind 4 (nonlinear Helmholtz)   u = (2 + x^2 + y^2 + z^2) sin(pi x) sin(pi y) sin(pi z)
           kind 5 (Lambda(u) = 1 + u^2)   u = (x + y + z) sin(pi x) sin(pi y) cos(pi z)   (Sec. 3.2)
           kind 6 (Lambda = 1 + |grad u|^2) u = sin(x(1-x)) sin(y(1-y)) e^(z + 1/2)
+          kind 7 (unit-ball diffusion-reaction) u = (x^2 + y^2 + z^2) sin(pi x) sin(pi y) sin(pi z)
         Each is a product form; the derivatives are written out by hand."""
         pi = math.pi
         x = [X[:, b] for b in range(3)]
@@ -206,8 +239,8 @@ class Problem:
             for c in range(3):
                 prod = prod * trig[c][1 if c == a else 0]
             dP[:, a] = prod
-        if self.kind == 4:
-            r = 2.0 + x[0] ** 2 + x[1] ** 2 + x[2] ** 2
+        if self.kind in (4, 7):
+            r = (2.0 if self.kind == 4 else 0.0) + x[0] ** 2 + x[1] ** 2 + x[2] ** 2
             dr = np.stack([2 * x[0], 2 * x[1], 2 * x[2]], axis=1)
             Hr = np.broadcast_to(2.0 * np.eye(3), (npts, 3, 3))
         else:
@@ -241,9 +274,11 @@ class Problem:
             for b in range(d):
                 S = S * np.sin(q * pi * X[:, b])
             return A * S
-        if k in (4, 5, 6):
+        if k in (4, 5, 6, 7):
             u, g, H = self.exact_jet(X)
             lap = H[:, 0, 0] + H[:, 1, 1] + H[:, 2, 2]
+            if k == 7:  # -div((1 + u^2) grad u) + u^3 - u + e^u
+                return (-(1.0 + u * u) * lap - 2.0 * u * np.einsum("ra,ra->r", g, g) + u ** 3 - u + np.exp(u))
             if k == 4:  # Lap u + p0 u + p1 cosh(u) = f
                 return lap + p[0] * u + p[1] * np.cosh(u)
             if k == 5:  # -div((1 + u^2) grad u) = -(1 + u^2) Lap u - 2 u |grad u|^2

@@ -351,6 +351,95 @@ rfm_status build_tables(rfm_problem* p, std::vector<RowSeg>& segs, std::vector<d
   return RFM_OK;
 }
 
+// Row tables of the unit-ball geometry (Sec. 6.2, diffusion-reaction on the
+// unit ball): the interior grid of every subdomain and the face grids of every
+// interface, in the order of the box layout, keeping the points with
+// x^2 + y^2 + z^2 < 1; then Dirichlet rows at the Fibonacci points of the unit
+// sphere, z_i = 1 - (2i + 1)/N, radius sqrt(1 - z_i^2), azimuth
+// i pi (3 - sqrt 5), grouped by the subdomain that contains them (floor of
+// the scaled coordinate, clamped).  pts [m][4], meta as in k_points.
+void build_ball_rows(rfm_problem* p, const std::vector<double>& Xh, std::vector<double>& pts,
+                     std::vector<int4>& meta) {
+  const rfm_problem_desc& d = p->desc;
+  const int nbp = p->nmaxbp;
+  auto grid_pt = [&](int b, int j, int pp, int q) {
+    const double a = Xh[b * nbp + j], c = Xh[b * nbp + j + 1];
+    if (pp == 0) return a;
+    if (pp == q - 1) return c;
+    return a + ((c - a) * (double)pp) / (double)(q - 1);
+  };
+  auto inside = [](const double* x) { return (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2] < 1.0; };
+  auto idx_of = [&](int e, int* idx) {
+    for (int b = 2; b >= 0; --b) {
+      idx[b] = e % p->N[b];
+      e /= p->N[b];
+    }
+  };
+  auto push = [&](const double* x, int kind, int field, int axis, int sord, int e0, int e1) {
+    pts.insert(pts.end(), {x[0], x[1], x[2], 0.0});
+    const int code = kind | (field << 4) | ((axis & 0xF) << 8) | (sord << 12);
+    meta.push_back(make_int4(code, e0, e1, 0));
+  };
+  for (int e = 0; e < p->G; ++e) {
+    int idx[3];
+    idx_of(e, idx);
+    for (int f = 0; f < p->fields; ++f)
+      for (int i0 = 0; i0 < d.q_int[0]; ++i0)
+        for (int i1 = 0; i1 < d.q_int[1]; ++i1)
+          for (int i2 = 0; i2 < d.q_int[2]; ++i2) {
+            const double x[3] = {grid_pt(0, idx[0], i0, d.q_int[0]), grid_pt(1, idx[1], i1, d.q_int[1]),
+                                 grid_pt(2, idx[2], i2, d.q_int[2])};
+            if (inside(x)) push(x, 0, f, -1, 0, e, -1);
+          }
+  }
+  p->m_int = (long long)meta.size();
+  for (int a = 0; a < 3; ++a)
+    for (int e = 0; e < p->G; ++e) {
+      int idx[3];
+      idx_of(e, idx);
+      if (idx[a] >= p->N[a] - 1) continue;
+      int nb[3] = {idx[0], idx[1], idx[2]};
+      nb[a] += 1;
+      const int e2 = (nb[0] * p->N[1] + nb[1]) * p->N[2] + nb[2];
+      const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;  // the two axes along the face, in order
+      for (int f = 0; f < p->fields; ++f)
+        for (int so = 0; so < d.cont_order; ++so)
+          for (int i0 = 0; i0 < d.q_iface[b0]; ++i0)
+            for (int i1 = 0; i1 < d.q_iface[b1]; ++i1) {
+              double x[3];
+              x[a] = Xh[a * nbp + idx[a] + 1];
+              x[b0] = grid_pt(b0, idx[b0], i0, d.q_iface[b0]);
+              x[b1] = grid_pt(b1, idx[b1], i1, d.q_iface[b1]);
+              if (inside(x)) push(x, 1, f, a, so, e, e2);
+            }
+    }
+  p->m_iface = (long long)meta.size() - p->m_int;
+  const long long N = d.n_sphere;
+  const double ga = 3.141592653589793 * (3.0 - sqrt(5.0));
+  std::vector<std::vector<long long>> by_owner(p->G);
+  std::vector<double> F(3 * N);
+  for (long long i = 0; i < N; ++i) {
+    const double z = 1.0 - (2.0 * (double)i + 1.0) / (double)N;
+    const double r = sqrt(1.0 - z * z);
+    const double th = (double)i * ga;
+    F[3 * i] = r * cos(th);
+    F[3 * i + 1] = r * sin(th);
+    F[3 * i + 2] = z;
+    int e = 0;
+    for (int b = 0; b < 3; ++b) {
+      long long t = (long long)floor((F[3 * i + b] - d.lo[b]) / (d.hi[b] - d.lo[b]) * (double)p->N[b]);
+      t = std::min<long long>(std::max<long long>(t, 0), p->N[b] - 1);
+      e = e * p->N[b] + (int)t;
+    }
+    by_owner[e].push_back(i);
+  }
+  for (int e = 0; e < p->G; ++e)
+    for (int f = 0; f < p->fields; ++f)
+      for (long long i : by_owner[e]) push(&F[3 * i], 2, f, -1, 0, e, -1);
+  p->m = (long long)meta.size();
+  p->m_bdy = p->m - p->m_int - p->m_iface;
+}
+
 rfm_status ensure_sketch(rfm_problem* p, long long s, int kind) {
   if (s < p->n) {
     g_err = "sketch rows must be >= n";
@@ -575,10 +664,19 @@ rfm_status lsqr(rfm_problem* p, const double* b, double eta, double conlim, long
   RFM_CHECK_LAUNCH();
   // chunks of iterations until the device sets done; replayed from a graph
   // unless LSQR's own kernels are being timed (event timing needs eager launches)
-  const bool graph = !rfm_prof_active((1u << PF_TRSV) | (1u << PF_JMV) | (1u << PF_JTMV) | (1u << PF_VECTOR));
+  bool graph = !p->lsqr_eager &&
+               !rfm_prof_active((1u << PF_TRSV) | (1u << PF_JMV) | (1u << PF_JTMV) | (1u << PF_VECTOR));
   p->skip = done;
   rfm_status r = RFM_OK;
-  if (graph) r = lsqr_graph(p, lst, done);
+  if (graph) {
+    r = lsqr_graph(p, lst, done);
+    if (r != RFM_OK) {  // capture or instantiation refused: run the same kernels eagerly from now on
+      cudaGetLastError();
+      p->lsqr_eager = true;
+      graph = false;
+      r = RFM_OK;
+    }
+  }
   int* hflag = (int*)p->hostbuf;
   for (long long chunks = 0; r == RFM_OK; ++chunks) {
     if (graph) {
@@ -771,8 +869,9 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
   const int D = desc->dim;
   if (D < 2 || D > 3 || desc->M <= 0 || desc->fields < 1 || desc->fields > RFM_MAX_FIELDS ||
       desc->cont_order < 1 || desc->cont_order > 2 || desc->fields * desc->M > RFM_MAX_WIDTH ||
-      desc->pde_kind < 0 || desc->pde_kind > 6 || (desc->pde_kind == 1 && (desc->fields != 2 || D != 3)) ||
-      (desc->pde_kind >= 4 && D != 3) || (desc->pde_kind != 1 && desc->fields != 1)) {
+      desc->pde_kind < 0 || desc->pde_kind > 7 || (desc->pde_kind == 1 && (desc->fields != 2 || D != 3)) ||
+      (desc->pde_kind >= 4 && D != 3) || (desc->pde_kind != 1 && desc->fields != 1) || desc->geometry < 0 ||
+      desc->geometry > 1 || (desc->geometry == 1 && (D != 3 || desc->n_sphere <= 0 || desc->n_sphere > (1 << 26)))) {
     g_err = "invalid problem description";
     return RFM_EINVAL;
   }
@@ -797,15 +896,29 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
   std::vector<double> Xh, muh, sgh;
   build_tables(p, segs, Xh, muh, sgh);
   p->nseg = (int)segs.size();
+  std::vector<double> ball_pts;
+  std::vector<int4> ball_meta;
+  if (desc->geometry == 1) {
+    build_ball_rows(p, Xh, ball_pts, ball_meta);
+    p->explicit_rows = true;
+  }
   // transposed block structure for J^T and the Gaussian sketch
   std::vector<int> colptr(p->G + 1, 0), colrows;
   {
     std::vector<std::vector<int>> lists(p->G);
-    for (const RowSeg& s : segs)
-      for (long long r = s.row0; r < s.row0 + s.count; ++r) {
-        lists[s.e0].push_back((int)r);
-        if (s.kind == 1) lists[s.e1].push_back((int)(r | 0x80000000u));
+    if (p->explicit_rows) {
+      for (long long r = 0; r < p->m; ++r) {
+        const int4 mt = ball_meta[r];
+        lists[mt.y].push_back((int)r);
+        if ((mt.x & 0xF) == 1) lists[mt.z].push_back((int)(r | 0x80000000u));
       }
+    } else {
+      for (const RowSeg& s : segs)
+        for (long long r = s.row0; r < s.row0 + s.count; ++r) {
+          lists[s.e0].push_back((int)r);
+          if (s.kind == 1) lists[s.e1].push_back((int)(r | 0x80000000u));
+        }
+    }
     for (int b = 0; b < p->G; ++b) {
       std::sort(lists[b].begin(), lists[b].end(),
                 [](int x, int y) { return (unsigned)(x & 0x7fffffff) < (unsigned)(y & 0x7fffffff); });
@@ -839,6 +952,7 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
     TRYA(dalloc(&p->hbuck, p->m));
     TRYA(dalloc(&p->hsign, p->m));
     TRYA(dalloc(&p->red, 4096));
+    TRYA(dalloc(&p->trsv_acc, (size_t)((p->n + 63) / 64) * 64));
     TRYA(dalloc(&p->sync, RFM_SYNC_WORDS));
     p->work_cap = vec_stride(p) * WV_COUNT;
     TRYA(dalloc(&p->work, p->work_cap));
@@ -860,6 +974,10 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
     CPY(p->segs, segs.data(), segs.size());
     CPY(p->colptr, colptr.data(), colptr.size());
     CPY(p->colrows, colrows.data(), colrows.size());
+    if (p->explicit_rows) {
+      CPY(p->pts, ball_pts.data(), ball_pts.size());
+      CPY(p->rmeta, ball_meta.data(), ball_meta.size());
+    }
 #undef CPY
     if (cudaMemsetAsync(p->sync, 0, RFM_SYNC_WORDS * sizeof(unsigned int), s0) != cudaSuccess) {
       st = RFM_ECUDA;
@@ -886,7 +1004,8 @@ rfm_status rfm_problem_destroy(rfm_problem* p) {
   else cudaDeviceSynchronize();
   void* bufs[] = {p->X, p->mu, p->sig, p->feat, p->segs, p->pts, p->rmeta, p->rhs, p->Jp, p->Js, p->lam, p->F,
                   p->colptr, p->colrows, p->B, p->Sg, p->hbuck, p->hsign, p->bptr, p->brows, p->Rown, p->work,
-                  p->red, p->sync, p->sdig, p->jdig, p->oz_e, p->oz_toff, p->qr_emu, p->qr_scratch};
+                  p->red, p->sync, p->sdig, p->jdig, p->oz_e, p->oz_toff, p->qr_emu, p->qr_scratch,
+                  p->trsv_acc};
   drop_lsqr_graph(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void* b : bufs) dfree(b);

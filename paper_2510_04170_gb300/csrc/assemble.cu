@@ -61,6 +61,7 @@ __device__ __forceinline__ double grid_pt(const double* X, int nbp, int b, int j
 //   kind 4  u = (2 + x^2 + y^2 + z^2) sin(pi x) sin(pi y) sin(pi z)
 //   kind 5  u = (x + y + z) sin(pi x) sin(pi y) cos(pi z)
 //   kind 6  u = sin(x(1-x)) sin(y(1-y)) e^(z + 1/2)
+//   kind 7  u = (x^2 + y^2 + z^2) sin(pi x) sin(pi y) sin(pi z)
 __device__ void exact_jet3(int kind, const double* x, double& u, double* g, double* h) {
   double f[3][3];  // factor b: value, first, second derivative
   if (kind == 6) {
@@ -99,8 +100,8 @@ __device__ void exact_jet3(int kind, const double* x, double& u, double* g, doub
   }
   // u = r P with r = 2 + |x|^2 (kind 4) or x + y + z (kind 5)
   double r, dr[3], hr;
-  if (kind == 4) {
-    r = 2.0 + x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  if (kind == 4 || kind == 7) {
+    r = (kind == 4 ? 2.0 : 0.0) + x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     for (int b = 0; b < 3; ++b) dr[b] = 2.0 * x[b];
     hr = 2.0;  // diagonal of Hess r; off-diagonal 0
   } else {
@@ -124,6 +125,7 @@ __device__ void exact_jet3(int kind, const double* x, double& u, double* g, doub
 //   kind 4  R = Lap u + p0 u + p1 cosh(u)                       (Sec. 6.2, Helmholtz)
 //   kind 5  R = -(1 + u^2) Lap u - 2 u |grad u|^2               (-div((1 + u^2) grad u))
 //   kind 6  R = -(1 + |g|^2) Lap u - 2 g^T H g                  (-div((1 + |grad u|^2) grad u))
+//   kind 7  kind 5 plus the reaction u^3 - u + e^u              (diffusion-reaction on the unit ball)
 __device__ __forceinline__ double jet_residual(const PdeConst& pc, const double* Q, double* C) {
   const double u = Q[0], g0 = Q[1], g1 = Q[2], g2 = Q[3];
   const double H00 = Q[4], H11 = Q[5], H22 = Q[6], H01 = Q[7], H02 = Q[8], H12 = Q[9];
@@ -136,14 +138,20 @@ __device__ __forceinline__ double jet_residual(const PdeConst& pc, const double*
     return lap + pc.p[0] * u + pc.p[1] * cosh(u);
   }
   const double gg = g0 * g0 + g1 * g1 + g2 * g2;
-  if (pc.kind == 5) {
+  if (pc.kind == 5 || pc.kind == 7) {
     const double L = 1.0 + u * u;
     C[0] = -2.0 * u * lap - 2.0 * gg;
     C[1] = -4.0 * u * g0;
     C[2] = -4.0 * u * g1;
     C[3] = -4.0 * u * g2;
     C[4] = C[5] = C[6] = -L;
-    return -L * lap - 2.0 * u * gg;
+    double R = -L * lap - 2.0 * u * gg;
+    if (pc.kind == 7) {  // reaction u^3 - u + e^u
+      const double eu = exp(u);
+      C[0] += 3.0 * u * u - 1.0 + eu;
+      R += u * u * u - u + eu;
+    }
+    return R;
   }
   const double L = 1.0 + gg;
   const double Hg0 = H00 * g0 + H01 * g1 + H02 * g2;
@@ -257,6 +265,18 @@ __global__ void k_points(const RowSeg* __restrict__ segs, int nseg, const double
   if (sg.kind == 0) r = source_term(pc, x, sg.field);
   else if (sg.kind == 2) r = exact_field(pc, x, sg.field);
   rhs[i] = r;
+}
+
+// Right-hand sides of rows whose points and metadata the host built (masked
+// geometries): the source f on interior rows, the Dirichlet data g on
+// boundary rows, 0 on interface rows.
+__global__ void k_rows_rhs(PdeConst pc, const double* __restrict__ pts, const int4* __restrict__ meta,
+                           double* __restrict__ rhs, long long m) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int code = meta[i].x, kind = code & 0xF, f = (code >> 4) & 0xF;
+  const double x[3] = {pts[4 * i], pts[4 * i + 1], pts[4 * i + 2]};
+  rhs[i] = kind == 0 ? source_term(pc, x, f) : (kind == 2 ? exact_field(pc, x, f) : 0.0);
 }
 
 // Nonlinear term N_f(u) of the row's field and its partial derivatives
@@ -680,8 +700,11 @@ rfm_status rfm_launch_setup(rfm_problem* p) {
                                                                      k1);
   RFM_CHECK_LAUNCH();
   PdeConst pc = make_pc(p);
-  k_points<<<grid_for(p->m, 256, 1 << 30), 256, 0, p->stream>>>(
-      p->segs, p->nseg, p->X, p->nmaxbp, pc, p->N[0], p->N[1], p->N[2], nullptr, p->pts, p->rmeta, p->rhs, p->m);
+  if (p->explicit_rows)  // points and metadata uploaded by the host: right-hand sides only
+    k_rows_rhs<<<grid_for(p->m, 256, 1 << 30), 256, 0, p->stream>>>(pc, p->pts, p->rmeta, p->rhs, p->m);
+  else
+    k_points<<<grid_for(p->m, 256, 1 << 30), 256, 0, p->stream>>>(
+        p->segs, p->nseg, p->X, p->nmaxbp, pc, p->N[0], p->N[1], p->N[2], nullptr, p->pts, p->rmeta, p->rhs, p->m);
   RFM_CHECK_LAUNCH();
   {  // once per device
     const int bytes = 4 * 2 * RFM_MAX_WIDTH * (int)sizeof(double);

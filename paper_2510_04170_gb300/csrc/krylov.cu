@@ -7,14 +7,22 @@
 //             rows touching the block are walked in a fixed order and the
 //             eight warps' partial sums are combined in a fixed order, so the
 //             result is deterministic.
-//  * k_trsv:  x = R^{-1} b or x = R^{-T} b for the upper-triangular
+//  * k_trsv_chain: x = R^{-1} b or x = R^{-T} b for the upper-triangular
 //             preconditioner R (column-major, leading dimension ldr), in one
-//             launch: 64-row blocks are claimed through a ticket counter in
+//             cooperative launch: one chain CTA solves the 64 x 64 diagonal
+//             blocks in dependency order from tiles it prefetched into shared
+//             memory, and helper CTAs stream the rest of R once, each adding
+//             the contributions of published blocks to the blocks it owns
+//             (details at the kernel).
+//  * k_trsv:  the same solve for sizes with more blocks than the helpers can
+//             own: 64-row blocks are claimed through a ticket counter in
 //             dependency order, each block waits (bounded) on the per-block
 //             flags of the blocks it needs, accumulates their contribution
 //             with coalesced column reads of R, solves its diagonal block in
 //             one warp and publishes its part of x with a release flag.
 //  * k_partial_* / k_finish_*: deterministic two-stage norms and dots.
+#include <algorithm>
+
 #include "rfm_internal.cuh"
 
 namespace {
@@ -188,6 +196,267 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
   }
 }
 
+// ---------------------------------------------------------------------------
+// Triangular solve as one chain CTA plus helper CTAs (cooperative launch, all
+// CTAs co-resident).  The 64-row blocks are solved in dependency order
+// t = 0, 1, ... (block nblk-1-t for R^{-1}, block t for R^{-T}).  The chain
+// CTA solves the diagonal blocks one after another; before step t it has the
+// diagonal tile and the tiles coupling block t to the two blocks solved just
+// before (order distance 1 and 2) in shared memory (cp.async, issued one step
+// ahead), so its step reads no global memory except the right-hand side and
+// one partial sum.  The helper CTAs add the contributions of all earlier
+// blocks (distance >= 3) as soon as each block is published: helper h owns
+// the targets t = 3 + (h - 1) + H m, streams their tiles of R (each read
+// once), and publishes each target's partial sum three steps before the
+// chain needs it.  All sums are in a fixed order, so results are
+// deterministic.  Waits are bounded (wait_flag).
+constexpr int TLD = TB + 1;            // leading dimension of a shared-memory tile (doubles)
+constexpr int TTILE = TB * TLD;        // doubles per shared-memory tile
+constexpr int CHAIN_NEAR = 3;          // the chain applies distances 1 .. CHAIN_NEAR-1 itself
+constexpr int HMAXT = 4;               // targets per helper CTA
+
+__host__ __device__ constexpr size_t chain_smem_bytes() {
+  return (size_t)(2 * 3 * TTILE + 3 * TB + TB + 8 * TB) * sizeof(double);
+}
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Tile of R with row block a and column block b into shared memory,
+// column-major with leading dimension TLD: T[cc * TLD + rr] = R(a*64 + rr, b*64 + cc).
+// Entries outside the n x n triangle's index range are zero.
+__device__ __forceinline__ void load_tile(double* T, const double* __restrict__ R, long long ldr, int n, int a,
+                                          int b) {
+  for (int idx = threadIdx.x; idx < TB * TB; idx += blockDim.x) {
+    const int rr = idx & (TB - 1), cc = idx >> 6;
+    const int gr = a * TB + rr, gc = b * TB + cc;
+    double* dst = T + cc * TLD + rr;
+    if (gr < n && gc < n) cp_async8(dst, R + (size_t)gc * ldr + gr);
+    else *dst = 0.0;
+  }
+}
+
+template <int TRANS>
+__device__ __forceinline__ int chain_block(int t, int nblk) { return TRANS == 0 ? nblk - 1 - t : t; }
+
+// Tiles of step t: the diagonal tile and the coupling tiles to the blocks of
+// order t-1 and t-2 (R(k, j) for R^{-1}: rows of block k, columns of block j;
+// R(j, k) for R^{-T}).
+template <int TRANS>
+__device__ __forceinline__ void chain_tiles(double* stage, const double* __restrict__ R, long long ldr, int n, int nblk,
+                                            int t) {
+  const int k = chain_block<TRANS>(t, nblk);
+  load_tile(stage, R, ldr, n, k, k);
+  for (int d = 1; d < CHAIN_NEAR; ++d) {
+    if (t - d < 0) break;
+    const int j = chain_block<TRANS>(t - d, nblk);
+    if (TRANS == 0) load_tile(stage + d * TTILE, R, ldr, n, k, j);
+    else load_tile(stage + d * TTILE, R, ldr, n, j, k);
+  }
+}
+
+struct ChainArgs {
+  const double* R;
+  long long ldr;
+  int n, nblk, H;
+  const double* rhs;
+  double* x;
+  double* accbuf;             // [nblk][64] helper partial sums
+  unsigned int* accflag;      // [nblk] epoch when accbuf[k] is complete
+  unsigned int* prog;         // number of blocks the chain has published (reset to 0 by k_trsv_prep)
+  const unsigned int* epoch_dev;
+  unsigned int* err;
+  const int* skip;
+};
+
+template <int TRANS>
+__global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) double csm[];
+  const unsigned int epoch = *a.epoch_dev;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nblk = a.nblk, n = a.n;
+  if (blockIdx.x == 0) {
+    // ------------------------------------------------------------ chain
+    double* stages = csm;                  // 2 stages x 3 tiles
+    double* xh = csm + 2 * 3 * TTILE;      // x of the last three steps [3][64]
+    double* srec = xh + 3 * TB;            // reciprocals of the diagonal [64]
+    double* sred = srec + TB;              // [8][64] partial sums
+    chain_tiles<TRANS>(stages, a.R, a.ldr, n, nblk, 0);
+    cp_async_commit();
+    for (int t = 0; t < nblk; ++t) {
+      double* st = stages + (t & 1) * 3 * TTILE;
+      if (t + 1 < nblk) chain_tiles<TRANS>(stages + ((t + 1) & 1) * 3 * TTILE, a.R, a.ldr, n, nblk, t + 1);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncthreads();
+      const int k = chain_block<TRANS>(t, nblk);
+      const int r0 = k * TB, rows = min(TB, n - r0);
+      if (tid < TB) srec[tid] = tid < rows ? 1.0 / st[tid * TLD + tid] : 0.0;
+      // contributions of the blocks at distance 1 and 2 (tiles in shared memory)
+      double p0 = 0.0, p1 = 0.0;
+      for (int d = 1; d < CHAIN_NEAR && t - d >= 0; ++d) {
+        const double* T = st + d * TTILE;
+        const double* xv = xh + ((t - d) % 3) * TB;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int y = w + 8 * q;
+          const double v = xv[y];
+          if (TRANS == 0) {  // target row lane / lane+32, source column y
+            p0 += T[y * TLD + lane] * v;
+            p1 += T[y * TLD + lane + 32] * v;
+          } else {           // target column lane / lane+32, source row y
+            p0 += T[lane * TLD + y] * v;
+            p1 += T[(lane + 32) * TLD + y] * v;
+          }
+        }
+      }
+      sred[w * TB + lane] = p0;
+      sred[w * TB + lane + 32] = p1;
+      // helper partial sums of the distances >= 3
+      if (t >= CHAIN_NEAR && tid == 0) wait_flag(a.accflag + k, epoch, a.err);
+      __syncthreads();
+      if (w == 0) {
+        double acc[2];
+        for (int h = 0; h < 2; ++h) {
+          const int rr = lane + 32 * h;
+          double sm = 0.0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) sm += sred[q * TB + rr];
+          if (t >= CHAIN_NEAR) sm += __ldcg(a.accbuf + (size_t)k * TB + rr);
+          acc[h] = rr < rows ? a.rhs[r0 + rr] - sm : 0.0;
+        }
+        const double* D = st;  // D(r, c) = D[c * TLD + r]
+        double xv[2] = {0.0, 0.0};
+        if (TRANS == 0) {
+          for (int i = rows - 1; i >= 0; --i) {
+            const int hh = i >> 5, ln = i & 31;
+            const double xi = __shfl_sync(0xffffffffu, acc[hh], ln) * srec[i];
+            if (lane == ln) xv[hh] = xi;
+            if (lane < i) acc[0] -= D[i * TLD + lane] * xi;
+            if (lane + 32 < i) acc[1] -= D[i * TLD + lane + 32] * xi;
+          }
+        } else {
+          for (int i = 0; i < rows; ++i) {
+            const int hh = i >> 5, ln = i & 31;
+            const double xi = __shfl_sync(0xffffffffu, acc[hh], ln) * srec[i];
+            if (lane == ln) xv[hh] = xi;
+            if (lane > i) acc[0] -= D[lane * TLD + i] * xi;
+            if (lane + 32 > i) acc[1] -= D[(lane + 32) * TLD + i] * xi;
+          }
+        }
+        double* xs = xh + (t % 3) * TB;
+        xs[lane] = xv[0];
+        xs[lane + 32] = xv[1];
+        if (lane < rows) a.x[r0 + lane] = xv[0];
+        if (lane + 32 < rows) a.x[r0 + lane + 32] = xv[1];
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(a.prog, (unsigned int)(t + 1));
+      }
+      __syncthreads();
+    }
+    cp_async_wait0();
+    return;
+  }
+  // -------------------------------------------------------------- helper
+  const int h = blockIdx.x - 1;
+  int tg[HMAXT], nt = 0;
+#pragma unroll
+  for (int m = 0; m < HMAXT; ++m) {
+    const int t = CHAIN_NEAR + h + a.H * m;
+    tg[m] = t < nblk ? t : -1;
+    if (t < nblk) nt = m + 1;
+  }
+  if (nt == 0) return;
+  const int tmax = tg[nt - 1];
+  double* tiles = csm;                   // [HMAXT] tiles
+  double* sred = csm + HMAXT * TTILE;    // [8][64]
+  double pa[HMAXT][2];                   // partial sums of rows lane, lane+32 (this warp's sources)
+#pragma unroll
+  for (int m = 0; m < HMAXT; ++m) pa[m][0] = pa[m][1] = 0.0;
+  for (int u = 0; u + CHAIN_NEAR <= tmax; ++u) {
+    const int j = chain_block<TRANS>(u, nblk);
+    // tiles first (they do not depend on x), then wait for block u
+#pragma unroll
+    for (int m = 0; m < HMAXT; ++m) {
+      if (m < nt && tg[m] >= u + CHAIN_NEAR) {
+        const int k = chain_block<TRANS>(tg[m], nblk);
+        if (TRANS == 0) load_tile(tiles + m * TTILE, a.R, a.ldr, n, k, j);
+        else load_tile(tiles + m * TTILE, a.R, a.ldr, n, j, k);
+      }
+    }
+    cp_async_commit();
+    if (tid == 0) {
+      // the progress counter only grows: wait until block u is published
+      const unsigned int want = (unsigned int)(u + 1);
+      const int lim = (int)__ldcg(a.err + (SYNC_WAITLIM - SYNC_ERR));
+      const unsigned int limit = lim == 0 ? (1u << 22) : (unsigned int)lim;
+      unsigned int spins = 0;
+      while (ld_acquire(a.prog) < want) {
+        if (lim < 0 || ++spins > limit) {
+          atomicExch(a.err, 1u);
+          break;
+        }
+        if (spins > (1u << 16)) __nanosleep(128);
+      }
+    }
+    cp_async_wait0();
+    __syncthreads();
+    const int c0 = j * TB;
+    double xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int y = w + 8 * q;
+      xv[q] = c0 + y < n ? __ldcg(a.x + c0 + y) : 0.0;
+    }
+#pragma unroll
+    for (int m = 0; m < HMAXT; ++m) {
+      if (!(m < nt && tg[m] >= u + CHAIN_NEAR)) continue;
+      const double* T = tiles + m * TTILE;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int y = w + 8 * q;
+        if (TRANS == 0) {
+          pa[m][0] += T[y * TLD + lane] * xv[q];
+          pa[m][1] += T[y * TLD + lane + 32] * xv[q];
+        } else {
+          pa[m][0] += T[lane * TLD + y] * xv[q];
+          pa[m][1] += T[(lane + 32) * TLD + y] * xv[q];
+        }
+      }
+    }
+    __syncthreads();  // tiles are refilled next step
+    // a target whose last helper source this was: publish its partial sum
+#pragma unroll
+    for (int m = 0; m < HMAXT; ++m) {
+      if (!(m < nt && tg[m] == u + CHAIN_NEAR)) continue;
+      const int k = chain_block<TRANS>(tg[m], nblk);
+      sred[w * TB + lane] = pa[m][0];
+      sred[w * TB + lane + 32] = pa[m][1];
+      __syncthreads();
+      if (w == 0) {
+        double* out = a.accbuf + (size_t)k * TB;
+        for (int hh = 0; hh < 2; ++hh) {
+          double sm = 0.0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) sm += sred[q * TB + lane + 32 * hh];
+          out[lane + 32 * hh] = sm;
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid == 0) st_release(a.accflag + k, epoch);
+    }
+  }
+}
+
 // Next epoch for the block flags (never 0, the initial flag value) and a fresh
 // ticket counter; runs before every k_trsv so that replays of a captured graph
 // see a new epoch each time.
@@ -283,6 +552,31 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
   RFM_CHECK_LAUNCH();
   ProfScope ps(PF_TRSV, p->stream);
   rfm_prof_work(PF_TRSV, 8.0 * (double)n * (n + 1) / 2 + 16.0 * n);  // R read once, b and x
+  // chain + helpers when every target past distance 2 has a helper slot
+  const int nsm = rfm_num_sms();
+  const int H = nblk > CHAIN_NEAR ? std::min(nsm - 1, nblk - CHAIN_NEAR) : 0;
+  if (p->trsv_acc && nsm > 1 && nblk - CHAIN_NEAR <= HMAXT * H) {
+    ChainArgs a;
+    a.R = p->R; a.ldr = p->ldr; a.n = n; a.nblk = nblk; a.H = H; a.rhs = b; a.x = x;
+    a.accbuf = p->trsv_acc; a.accflag = p->sync + SYNC_FLAGS; a.prog = p->sync + SYNC_TICKET;
+    a.epoch_dev = p->sync + SYNC_EPOCH; a.err = p->sync + SYNC_ERR; a.skip = p->skip;
+    const void* fn = trans == 0 ? (const void*)k_trsv_chain<0> : (const void*)k_trsv_chain<1>;
+    RFM_CUDA(rfm_smem_attr(fn, (int)chain_smem_bytes()));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(1 + H));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = chain_smem_bytes();
+    cfg.stream = p->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident: helpers and the chain wait on each other
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (trans == 0) RFM_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_chain<0>, a));
+    else RFM_CUDA(cudaLaunchKernelEx(&cfg, k_trsv_chain<1>, a));
+    RFM_CHECK_LAUNCH();
+    return RFM_OK;
+  }
   if (trans == 0)
     k_trsv<0><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->sync + SYNC_EPOCH,
                                            p->sync + SYNC_TICKET, p->sync + SYNC_ERR, p->skip);

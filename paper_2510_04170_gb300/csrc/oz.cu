@@ -144,6 +144,30 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// All eight levels of 8 columns with one wait: the loads are issued back to
+// back, then one tcgen05.wait::ld; the empty asm statements after the wait
+// take the loaded registers as operands, so no use of them can be scheduled
+// before the wait.  Levels >= nlev (never written by the MMA) read as 0.
+__device__ __forceinline__ void tmem_levels_all(uint32_t cbase, int nlev, uint32_t (&r)[MAXD][8]) {
+#pragma unroll
+  for (int l = 0; l < MAXD; ++l) {
+    if (l < nlev) {
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]), "=r"(r[l][5]),
+                     "=r"(r[l][6]), "=r"(r[l][7])
+                   : "r"(cbase + (uint32_t)(l * BN)));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) r[l][i] = 0u;
+    }
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int l = 0; l < MAXD; ++l)
+    asm volatile("" : "+r"(r[l][0]), "+r"(r[l][1]), "+r"(r[l][2]), "+r"(r[l][3]), "+r"(r[l][4]), "+r"(r[l][5]),
+                 "+r"(r[l][6]), "+r"(r[l][7]));
+}
+
 // Levels l0 .. l0+3 of 8 columns (levels >= nlev read as 0) combined exactly,
 // L_l0 2^(3 BETA) + L_(l0+1) 2^(2 BETA) + L_(l0+2) 2^BETA + L_(l0+3), and
 // added to acc[0..7].  (Ten warps leave 168 registers a thread, which the
@@ -361,7 +385,77 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
     unsigned cglob = 0;
     bool alive = true;
-    for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
+    if (nchunks == 1) {
+      // One 512-deep chunk per tile (K <= 512: the QR trailing update).  Per
+      // group of 8 columns all levels are loaded with one wait; C and the
+      // column exponents of the next group are loaded while this group is
+      // combined; the accumulators are released as soon as the last group's
+      // levels are in registers, so the next tile's MMAs overlap the rest.
+      for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
+        const int mt = t % g.mtiles, nt = t / g.mtiles;
+        const long long gi = (long long)mt * BM + row;
+        const bool rin = gi < g.M;
+        const int ei = rin ? __ldg(g.ea + gi) : 0;
+        double cn[8];
+        int ebn[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const long long gj = (long long)nt * BN + col0 + i;
+          const bool in = rin && gj < g.N;
+          ebn[i] = gj < g.N ? __ldg(g.eb + gj) : 0;
+          cn[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
+        }
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, cglob & 1, g.err, 9));
+        tc_fence_after();
+        if (!ok) {
+          alive = false;
+          break;
+        }
+#pragma unroll 1
+        for (int grp = 0; grp < EPI_COLS / 8; ++grp) {
+          uint32_t r[MAXD][8];
+          tmem_levels_all(tmem + tlane + (uint32_t)(col0 + grp * 8), nlev, r);
+          if (grp == EPI_COLS / 8 - 1) {  // every level of this warp's columns is in registers
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->acc_empty);
+            ++cglob;
+          }
+          double cc[8];
+          int eb[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            cc[i] = cn[i];
+            eb[i] = ebn[i];
+          }
+          if (grp + 1 < EPI_COLS / 8) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const long long gj = (long long)nt * BN + col0 + (grp + 1) * 8 + i;
+              const bool in = rin && gj < g.N;
+              ebn[i] = gj < g.N ? __ldg(g.eb + gj) : 0;
+              cn[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
+            }
+          }
+          if (rin) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              long long hi = 0, lo = 0;
+#pragma unroll
+              for (int l = 0; l < 4; ++l) hi = (hi << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
+#pragma unroll
+              for (int l = 4; l < MAXD; ++l) lo = (lo << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
+              const long long gj = (long long)nt * BN + col0 + grp * 8 + i;
+              if (gj < g.N) {
+                const double val = fix_to_double(hi, lo, ei + eb[i] - 9 * BETA);
+                g.C[gi + gj * g.ldc] = g.mode == 0 ? val : cc[i] - val;
+              }
+            }
+          }
+        }
+      }
+    }
+    for (int t = blockIdx.x; t < ntiles_total && alive && nchunks > 1; t += gridDim.x) {
       const int mt = t % g.mtiles, nt = t / g.mtiles;
       if (g.mode != 0) {  // C is read in the final update: start bringing it into L2 now
         const long long gi = (long long)mt * BM + row;

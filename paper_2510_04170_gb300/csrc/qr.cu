@@ -5,10 +5,12 @@
 //   for each panel of NB columns:
 //     k_panel   (cooperative, one CTA per SM slice of rows): the panel's rows
 //               stay in shared memory; per column one bounded grid barrier
-//               combines the column norm, a second combines v^T A for the rest
-//               of the panel.  Reflector H = I - tau v v^T, v_0 = 1,
-//               beta = -sign(alpha) ||x||.  At the end T (NB x NB, upper) with
-//               T_jj = tau_j, T_{:j,j} = -tau_j T_{:j,:j} V_{:,:j}^T v_j.
+//               combines the column norm below the pivot and the products of
+//               the unscaled column with the rest of the panel, from which
+//               every CTA forms v^T A (details at the kernel).  Reflector
+//               H = I - tau v v^T, v_0 = 1, beta = -sign(alpha) ||x||.  At the
+//               end T (NB x NB, upper) with T_jj = tau_j,
+//               T_{:j,j} = -tau_j T_{:j,:j} V_{:,:j}^T v_j.
 //     k_vta     W_z = V^T A_trail over a K-slice z (split K, deterministic)
 //     k_wt      W2 = T^T sum_z W_z
 //     k_update  A_trail -= V W2
@@ -34,9 +36,9 @@ struct PanelArgs {
   long long s;
   long long j0;
   int nbw;           // columns in this panel (<= NB)
-  int P;             // CTAs
+  int P;             // CTAs (<= 256)
   int chunk;         // rows per CTA
-  double* part;      // [P][NB + 2]
+  double* part;      // two buffers of [512][NB + 2] partials (row 511 of each: the pivot row)
   double* gram;      // [P][NB*NB]
   double* tau;       // [n]
   double* T;         // [NB][NB] (row-major T[i][j])
@@ -61,26 +63,36 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, unsigned int nbl
   __syncthreads();
 }
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-    r = warp_sum(r);
-    if (lane == 0) sh[32] = r;
+// Sum over the P CTAs of partial value idx (stride NB + 2 per CTA) in a fixed
+// order: each lane loads its CTAs' values (all loads issued before the adds),
+// then the lanes are combined by the warp's butterfly.  Every CTA obtains
+// bitwise the same result.
+__device__ __forceinline__ double sum_partials(const double* part, int P, int idx, int lane) {
+  double t[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int q = lane + 32 * u;
+    t[u] = q < P ? __ldcg(part + q * (NB + 2) + idx) : 0.0;
   }
-  __syncthreads();
-  return sh[32];
+  double s = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) s += t[u];
+  return warp_sum(s);
 }
 
+// One grid-wide barrier per column.  Before it, every CTA contributes, for
+// its rows below the pivot row j, sigma = sum x_r^2 and p_k = sum x_r A_rk for
+// the remaining panel columns k (x = column j, not yet scaled); the CTA that
+// holds row j also publishes alpha = A_jj and the pivot row A_jk.  After it,
+// every CTA forms beta, tau, 1/(alpha - beta) and
+//     w_k = v^T A_k = A_jk + p_k / (alpha - beta)     (v_j = 1, v_r = x_r / (alpha - beta)),
+// the same quantities the two-barrier form obtains by reducing v^T A_k after
+// scaling.  The partials alternate between two buffers, so a CTA that runs
+// ahead into column j + 1 never overwrites values another CTA still reads.
 __global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
   extern __shared__ double sp[];  // [NB][chunk] column-major panel slice
-  __shared__ double sh[40];
-  __shared__ double sw[NB];
+  __shared__ double sw[NB];       // w_k, then tau w_k
+  __shared__ double sv[NB + 2];   // reduced sigma and p_k
   const int c = blockIdx.x;
   const long long rbeg = a.j0 + (long long)c * a.chunk;
   const long long rend = min(a.s, rbeg + a.chunk);
@@ -95,34 +107,26 @@ __global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
   for (int jj = 0; jj < a.nbw; ++jj) {
     const long long j = a.j0 + jj;  // pivot row
     double* v = sp + jj * chunk;
-    double loc = 0.0;
-    for (int r = tid; r < nr; r += blockDim.x)
-      if (rbeg + r > j) loc += v[r] * v[r];
-    loc = block_sum(loc, sh);
-    if (tid == 0) {
-      const bool own = j >= rbeg && j < rend;
-      a.part[c * (NB + 2) + 0] = loc;
-      a.part[c * (NB + 2) + 1] = own ? v[j - rbeg] : 0.0;
+    const int rest = a.nbw - jj - 1;
+    double* part = a.part + (size_t)(jj & 1) * 512 * (NB + 2);  // [P][NB + 2] this column's partials
+    double* piv = part + (size_t)511 * (NB + 2);                 // alpha, A_jk of the pivot row
+    // local partials: slot 0 sigma (kk = -1), slot 1 + kk p_k; one warp per slot
+    for (int kk = w - 1; kk < rest; kk += (blockDim.x >> 5)) {
+      const double* ck = kk < 0 ? v : sp + (jj + 1 + kk) * chunk;
+      double acc = 0.0;
+      for (int r = lane; r < nr; r += 32)
+        if (rbeg + r > j) acc += v[r] * ck[r];
+      acc = warp_sum(acc);
+      if (lane == 0) part[c * (NB + 2) + 1 + kk] = acc;
     }
+    if (j >= rbeg && j < rend && tid <= rest) piv[tid] = sp[(jj + tid) * chunk + (j - rbeg)];
     grid_barrier(a.bar, a.P, a.err);
-    // sigma and alpha over all CTAs: warp 0 loads the partials lane-strided
-    // (all loads in flight at once) and sums them in a fixed order, so every
-    // CTA obtains bitwise the same values
-    if (w == 0) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int q = lane; q < a.P; q += 32) {
-        s0 += __ldcg(a.part + q * (NB + 2));
-        s1 += __ldcg(a.part + q * (NB + 2) + 1);
-      }
-      s0 = warp_sum(s0);
-      s1 = warp_sum(s1);
-      if (lane == 0) {
-        sh[33] = s0;
-        sh[34] = s1;
-      }
+    for (int idx = w; idx <= rest; idx += (blockDim.x >> 5)) {
+      const double sm = sum_partials(part, a.P, idx, lane);
+      if (lane == 0) sv[idx] = sm;
     }
     __syncthreads();
-    const double sigma = sh[33], alpha = sh[34];
+    const double sigma = sv[0], alpha = __ldcg(piv);
     double tau = 0.0, beta = alpha, scale = 0.0;
     if (sigma != 0.0) {
       const double nrm = sqrt(alpha * alpha + sigma);
@@ -130,35 +134,15 @@ __global__ void __launch_bounds__(256) k_panel(PanelArgs a) {
       tau = (beta - alpha) / beta;
       scale = 1.0 / (alpha - beta);
     }
+    if (tid < rest) sw[tid] = tau * (__ldcg(piv + 1 + tid) + scale * sv[1 + tid]);  // tau w_k
     // v_r = x_r / (alpha - beta) below the pivot, v_j = 1
     if (tau != 0.0)
       for (int r = tid; r < nr; r += blockDim.x)
         if (rbeg + r > j) v[r] *= scale;
     __syncthreads();
-    // partial w_k = sum_{r >= j} v_r A[r, k] for the remaining panel columns
-    const int rest = a.nbw - jj - 1;
-    for (int kk = w; kk < rest; kk += (blockDim.x >> 5)) {
-      const double* ck = sp + (jj + 1 + kk) * chunk;
-      double acc = 0.0;
-      for (int r = lane; r < nr; r += 32) {
-        const long long gr = rbeg + r;
-        if (gr >= j) acc += (gr == j ? 1.0 : v[r]) * ck[r];
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) a.part[c * (NB + 2) + 2 + kk] = acc;
-    }
-    grid_barrier(a.bar, a.P, a.err);
-    // w_k over all CTAs: one warp per k, partials loaded lane-strided
-    for (int kk = w; kk < rest; kk += (blockDim.x >> 5)) {
-      double s = 0.0;
-      for (int q = lane; q < a.P; q += 32) s += __ldcg(a.part + q * (NB + 2) + 2 + kk);
-      s = warp_sum(s);
-      if (lane == 0) sw[kk] = s;
-    }
-    __syncthreads();
     if (tau != 0.0) {
       for (int kk = 0; kk < rest; ++kk) {
-        const double f = tau * sw[kk];
+        const double f = sw[kk];
         double* ck = sp + (jj + 1 + kk) * chunk;
         for (int r = tid; r < nr; r += blockDim.x) {
           const long long gr = rbeg + r;
@@ -441,7 +425,7 @@ rfm_status factor_range(double* A, long long s, long long lda, long long c0, lon
     // rows per CTA: at least 64, at most what fits in 200 KB of shared memory
     const long long maxchunk = (200LL * 1024) / (NB * (long long)sizeof(double));
     const long long cap = panel_cap > 0 ? std::min(panel_cap, nsm) : nsm;
-    long long P = std::min<long long>((rows + 63) / 64, cap);
+    long long P = std::min<long long>(std::min<long long>((rows + 63) / 64, cap), 256);  // k_panel sums <= 256 partials
     if (P < 1) P = 1;
     long long chunk = (rows + P - 1) / P;
     if (chunk > maxchunk && cap < nsm) {  // the cap would overflow shared memory: take the fewest CTAs that fit

@@ -43,6 +43,7 @@ struct rfm_problem {
   double* feat = nullptr;   // [G*fields*M][4]
   RowSeg* segs = nullptr;
   int nseg = 0;
+  bool explicit_rows = false;  // geometry with masked grids: points and row metadata built on the host
   double* pts = nullptr;    // [m][4]
   int4* rmeta = nullptr;    // per row: {kind|field<<4|axis<<8|sord<<12|side<<16, e0, e1, 0}
   double* rhs = nullptr;    // [m] source f (interior) or boundary data g
@@ -94,7 +95,9 @@ struct rfm_problem {
   cudaStream_t cap_stream = nullptr;  // private stream the chunk is captured on
   unsigned long long lsqr_graph_key = 0;
   long long lsqr_graph_launches = 0;  // kernels per chunk (launch accounting)
+  bool lsqr_eager = false;        // graph capture failed once: replay the chunk's kernels eagerly
   int qr_panel_cap = 0;           // most CTAs per panel factorisation (0: one per SM)
+  double* trsv_acc = nullptr;     // [ceil(n/64)][64] partial sums of the triangular solve's helpers
   // per-problem QR scratch (FP64 panel buffers)
   double* qr_scratch = nullptr;
   long long qr_scratch_len = 0;

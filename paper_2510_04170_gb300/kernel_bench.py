@@ -75,7 +75,8 @@ def main():
                    bf16_pair_tflops=36 * fl / ms / 1e9)
     elif a.what == "trsv":
         import rfm_workloads as W
-        desc = {"c2": W.config_c2, "c1": W.config_c1}[a.workload]()
+        desc = {"c2": W.config_c2, "c1": W.config_c1,
+                "n16k": lambda: W.problem(3, (4, 4, 4), 256, (6, 6, 6), (3, 3, 3), (3, 3, 3))}[a.workload]()
         gp = rfm.Problem(desc)
         n = gp.n
         R = torch.randn(n, n, dtype=torch.float64, device="cuda").triu_() / n ** 0.5

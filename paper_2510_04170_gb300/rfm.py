@@ -37,7 +37,8 @@ class ProblemDesc(ctypes.Structure):
                 ("nsub", ctypes.c_int * 3), ("M", ctypes.c_int), ("fields", ctypes.c_int),
                 ("q_int", ctypes.c_int * 3), ("q_bdy", ctypes.c_int * 3), ("q_iface", ctypes.c_int * 3),
                 ("cont_order", ctypes.c_int), ("feat_range", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("pde_kind", ctypes.c_int), ("pde_params", ctypes.c_double * 8)]
+                ("pde_kind", ctypes.c_int), ("pde_params", ctypes.c_double * 8), ("geometry", ctypes.c_int),
+                ("n_sphere", ctypes.c_int64)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -161,6 +162,8 @@ def make_desc(d):
     D.feat_range, D.seed, D.pde_kind = d["feat_range"], d["seed"], d["pde_kind"]
     for i in range(8):
         D.pde_params[i] = d["pde_params"][i]
+    D.geometry = {"box": 0, "ball": 1}[d.get("geometry", "box")]
+    D.n_sphere = int(d.get("n_sphere", 0))
     return D
 
 

@@ -22,6 +22,10 @@ those of the configurations C1-C5 below):
               (Sec. 3.2 benchmark)
   pde_kind 6  -div((1 + |grad u|^2) grad u) = f on [0,1]^3,
               u* = sin(x(1-x)) sin(y(1-y)) e^(z+1/2)  (Sec. 6.2, strongly nonlinear)
+  pde_kind 7  -div((1 + u^2) grad u) + u^3 - u + e^u = f on the unit ball,
+              u* = |x|^2 prod sin(pi x_d)  (Sec. 6.2, diffusion-reaction on the ball:
+              geometry "ball", the cube [-1,1]^3 in subdomains, collocation points
+              inside the ball kept, Dirichlet rows at n_sphere Fibonacci points)
 """
 from __future__ import annotations
 
@@ -55,7 +59,7 @@ def problem(dim, nsub, M, q_int, q_bdy, q_iface, *, fields=1, lo=None, hi=None,
 
 def _default_params(kind):
     return {0: [1.0], 1: [2e-3, 1e-3, 0.04, 0.06], 2: [1.0], 3: [1.0, 1.0, 1.0], 4: [-100.0, 10.0],
-            5: [], 6: []}[kind]
+            5: [], 6: [], 7: []}[kind]
 
 
 def solve_opts(**kw):
@@ -113,6 +117,16 @@ def operator_small(kind):
     return problem(3, (2, 2, 2), 100, (8, 8, 8), (8, 8, 8), (8, 8, 8), pde_kind=kind)
 
 
+def ball(M, q, n_sphere, nsub=(2, 2, 2)):
+    """Unit-ball diffusion-reaction (kind 7): [-1,1]^3 in nsub subdomains, q^3
+    grid points per subdomain and q x q per interface (those inside the ball
+    kept), n_sphere Fibonacci points on the sphere."""
+    d = problem(3, nsub, M, (q, q, q), (q, q, q), (q, q, q), lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
+                pde_kind=7)
+    d.update(geometry="ball", n_sphere=int(n_sphere))
+    return d
+
+
 def config_c5(kappa=1.0, amp=1.0, freq=1.0):
     """Learned-warm-start family: 2x2x2 subdomains, M=512 (n=4,096)."""
     return problem(3, (2, 2, 2), 512, (12, 12, 12), (6, 6, 6), (6, 6, 6),
@@ -161,6 +175,16 @@ def random_points(desc, count, seed=11):
     d = desc["dim"]
     lo = np.array(desc["lo"][:d]); hi = np.array(desc["hi"][:d])
     return lo + (hi - lo) * rng.random((count, d))
+
+
+def ball_points(count, seed=5):
+    """`count` seeded uniform points inside the unit ball (rejection from the cube)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while sum(len(o) for o in out) < count:
+        P = rng.uniform(-1.0, 1.0, (2 * count, 3))
+        out.append(P[np.sum(P * P, axis=1) < 1.0])
+    return np.concatenate(out)[:count]
 
 
 def eval_grid(desc, per_axis=10):

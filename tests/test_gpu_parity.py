@@ -54,6 +54,7 @@ CASES = {
     "3d_helmholtz": W.small_3d(pde_kind=4, M=20),
     "3d_quasilinear": W.small_3d(pde_kind=5, M=20),
     "3d_strongly_nonlinear": W.small_3d(pde_kind=6, M=20),
+    "3d_ball": W.ball(20, 7, 300),
 }
 
 
@@ -224,7 +225,7 @@ def test_lsqr_direction(name):
 
 
 @pytest.mark.parametrize("name", ["2d_c1", "3d_small", "3d_grayscott", "3d_helmholtz", "3d_quasilinear",
-                                  "3d_strongly_nonlinear"])
+                                  "3d_strongly_nonlinear", "3d_ball"])
 def test_linesearch(name):
     desc = CASES[name]
     op = OProblem(desc)

@@ -6,6 +6,8 @@ stored by the committed scripts in tests/golden/ (they call only the oracle):
   * the three further operators of Sec. 3.2 / Sec. 6.2 (nonlinear Helmholtz,
     -div((1+u^2) grad u), -div((1+|grad u|^2) grad u)) at 2x2x2 subdomains,
     M = 100, IPN and AMIPN;
+  * the diffusion-reaction equation on the unit ball (Sec. 6.2: masked grids,
+    Fibonacci boundary points), 2x2x2 subdomains, M = 100, AMIPN and IPN;
   * the 3D benchmark solve (4x4x4 subdomains, M = 512, n = 32,768, Gaussian
     sketch of 65,536 rows) in the configuration the benchmark times
     (tensor-core sketch and QR update), IPN.
@@ -74,3 +76,15 @@ def test_benchmark_solve_matches_oracle(rfm):
     gp = rfm.Problem(desc)
     c, info = gp.rfm_ipn_solve(W.opts_c2(precision=2))
     _check(gp, c, info, ref["u"], ref["outer_iters"], ref["n_jac"], ref["lsqr_iters"], W.eval_grid(desc))
+
+
+@pytest.mark.parametrize("solver", ["amipn", "ipn"])
+def test_ball_solve_matches_oracle(rfm, solver):
+    """Diffusion-reaction on the unit ball (Sec. 6.2): masked grids and
+    Fibonacci boundary points."""
+    ref = np.load(os.path.join(GOLDEN, "ball_oracle.npz"))
+    desc = W.ball(100, 10, 2000)
+    gp = rfm.Problem(desc)
+    c, info = getattr(gp, f"rfm_{solver}_solve")(W.solve_opts())
+    _check(gp, c, info, ref[f"{solver}_u"], ref[f"{solver}_outer_iters"], ref[f"{solver}_n_jac"],
+           ref[f"{solver}_lsqr_iters"], ref["X"])

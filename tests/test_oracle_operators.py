@@ -1,7 +1,9 @@
-"""Pins of the oracle's three further operators of the paper (Sec. 3.2 and
-Sec. 6.2): the nonlinear Helmholtz equation Lap u - 100 u + 10 cosh u = f
-(kind 4), the quasi-linear -div((1 + u^2) grad u) = f (kind 5) and the
-strongly nonlinear -div((1 + |grad u|^2) grad u) = f (kind 6).
+"""Pins of the oracle's further operators of the paper (Sec. 3.2 and Sec.
+6.2): the nonlinear Helmholtz equation Lap u - 100 u + 10 cosh u = f (kind
+4), the quasi-linear -div((1 + u^2) grad u) = f (kind 5), the strongly
+nonlinear -div((1 + |grad u|^2) grad u) = f (kind 6) and the unit-ball
+diffusion-reaction -div((1 + u^2) grad u) + u^3 - u + e^u = f (kind 7), with
+the unit-ball geometry (masked grids, Fibonacci boundary points).
 
 Each closed form is checked against something it does not share code with:
 the Jacobian against central differences of the residual, the manufactured
@@ -16,7 +18,7 @@ import rfm_workloads as W
 from oracle import assemble as asm
 from oracle.problem import Problem
 
-KINDS = (4, 5, 6)
+KINDS = (4, 5, 6, 7)
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -123,6 +125,47 @@ def test_manufactured_sources_satisfy_the_pdes():
     ref = -_div_fd(flux6, X, h)
     f = p.source(X, 0)
     assert np.max(np.abs(f - ref)) < 1e-4 * np.abs(ref).max()
+    # kind 7: kind 5's flux form plus the reaction u^3 - u + e^u
+    p = Problem(W.small_3d(pde_kind=7, M=8))
+    u = _u(p)
+    flux = lambda Y: (1.0 + u(Y) ** 2)[:, None] * _grad_fd(u, Y, h)
+    ref = -_div_fd(flux, X, h) + u(X) ** 3 - u(X) + np.exp(u(X))
+    f = p.source(X, 0)
+    assert np.max(np.abs(f - ref)) < 1e-4 * np.abs(ref).max()
+
+
+def test_fibonacci_points_cover_the_sphere_evenly():
+    from oracle.problem import fibonacci_sphere
+    N = 4000
+    F = fibonacci_sphere(N)
+    assert np.max(np.abs(np.linalg.norm(F, axis=1) - 1.0)) < 1e-15
+    # equal-area property: every octant holds about N / 8 points, and the
+    # z-coordinates are uniform on (-1, 1) (Archimedes: equal z-bands, equal area)
+    octant = (F[:, 0] > 0) * 4 + (F[:, 1] > 0) * 2 + (F[:, 2] > 0)
+    counts = np.bincount(octant, minlength=8)
+    assert np.all(np.abs(counts - N / 8) < 0.03 * N / 8)
+    assert np.allclose(np.sort(F[:, 2]), np.linspace(1 - 1 / N, -1 + 1 / N, N)[::-1])
+    # no two points closer than a fraction of the mean spacing sqrt(4 pi / N)
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(F).query(F, k=2)
+    assert d[:, 1].min() > 0.5 * np.sqrt(4 * np.pi / N)
+
+
+def test_ball_rows():
+    d = W.ball(20, 7, 500)
+    p = Problem(d)
+    r2 = np.sum(p.rx ** 2, axis=1)
+    interior = slice(0, p.m_int + p.m_iface)
+    assert np.all(r2[interior] < 1.0)
+    assert p.m_bdy == 500 and np.allclose(r2[p.m_int + p.m_iface:], 1.0, rtol=0, atol=1e-15)
+    # every row lies in (the closure of) its subdomain
+    lo = p.mu[p.re0] - p.sigma[p.re0]
+    hi = p.mu[p.re0] + p.sigma[p.re0]
+    assert np.all((p.rx >= lo - 1e-15) & (p.rx <= hi + 1e-15))
+    # the same grids as the box layout, minus the points outside the ball
+    box = Problem(W.with_(d, geometry="box"))
+    kept = np.sum(np.sum(box.rx[:box.m_int] ** 2, axis=1) < 1.0)
+    assert kept == p.m_int
 
 
 @pytest.mark.parametrize("kind", KINDS)
