@@ -173,6 +173,13 @@ rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, doub
  * column-major) receives a copy. */
 rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev);
 
+/* Replaces the right-hand sides of the system (Alg. 3: the source f at the
+ * interior rows, the Dirichlet data g at the boundary rows) with rhs_dev [m]
+ * in row order; interface rows carry no data and stay 0.  By default a
+ * problem uses the manufactured data of its pde_kind.  The residual is
+ * F_i = (operator row) - rhs_i. */
+rfm_status rfm_set_rhs(rfm_problem* p, const double* rhs_dev);
+
 /* Limit on the device-side polls of the bounded flag waits (the grid barriers
  * of the QR panel factorisation and the block flags of the triangular solves)
  * of this problem: 0 restores the default (2^22 polls), a positive count sets

@@ -1087,6 +1087,18 @@ rfm_status rfm_residual(rfm_problem* p, const double* c_dev, double* F_dev, doub
   return RFM_OK;
 }
 
+rfm_status rfm_set_rhs(rfm_problem* p, const double* rhs_dev) {
+  if (!p || !rhs_dev) {
+    g_err = "rfm_set_rhs: null argument";
+    return RFM_EINVAL;
+  }
+  RFM_CUDA(cudaMemcpyAsync(p->rhs, rhs_dev, (size_t)p->m * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  if (p->m_iface)  // interface rows have no data: keep them at zero
+    RFM_CUDA(cudaMemsetAsync(p->rhs + p->m_int, 0, (size_t)p->m_iface * sizeof(double), p->stream));
+  RFM_CUDA(cudaStreamSynchronize(p->stream));
+  return RFM_OK;
+}
+
 rfm_status rfm_set_wait_limit(rfm_problem* p, int64_t polls) {
   if (!p) {
     g_err = "rfm_set_wait_limit: null problem";

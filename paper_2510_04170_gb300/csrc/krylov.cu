@@ -232,8 +232,8 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // column-major with leading dimension TLD: T[cc * TLD + rr] = R(a*64 + rr, b*64 + cc).
 // Entries outside the n x n triangle's index range are zero.
 __device__ __forceinline__ void load_tile(double* T, const double* __restrict__ R, long long ldr, int n, int a,
-                                          int b) {
-  for (int idx = threadIdx.x; idx < TB * TB; idx += blockDim.x) {
+                                          int b, int first, int stride) {
+  for (int idx = first; idx < TB * TB; idx += stride) {
     const int rr = idx & (TB - 1), cc = idx >> 6;
     const int gr = a * TB + rr, gc = b * TB + cc;
     double* dst = T + cc * TLD + rr;
@@ -247,17 +247,21 @@ __device__ __forceinline__ int chain_block(int t, int nblk) { return TRANS == 0 
 
 // Tiles of step t: the diagonal tile and the coupling tiles to the blocks of
 // order t-1 and t-2 (R(k, j) for R^{-1}: rows of block k, columns of block j;
-// R(j, k) for R^{-T}).
+// R(j, k) for R^{-T}).  Issued by warps 1-7 only: warp 0 publishes each
+// step's result behind a memory fence, which would otherwise also wait for
+// these copies in flight.
 template <int TRANS>
 __device__ __forceinline__ void chain_tiles(double* stage, const double* __restrict__ R, long long ldr, int n, int nblk,
                                             int t) {
+  if (threadIdx.x < 32) return;
+  const int first = threadIdx.x - 32, stride = blockDim.x - 32;
   const int k = chain_block<TRANS>(t, nblk);
-  load_tile(stage, R, ldr, n, k, k);
+  load_tile(stage, R, ldr, n, k, k, first, stride);
   for (int d = 1; d < CHAIN_NEAR; ++d) {
     if (t - d < 0) break;
     const int j = chain_block<TRANS>(t - d, nblk);
-    if (TRANS == 0) load_tile(stage + d * TTILE, R, ldr, n, k, j);
-    else load_tile(stage + d * TTILE, R, ldr, n, j, k);
+    if (TRANS == 0) load_tile(stage + d * TTILE, R, ldr, n, k, j, first, stride);
+    else load_tile(stage + d * TTILE, R, ldr, n, j, k, first, stride);
   }
 }
 
@@ -334,8 +338,12 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         }
         const double* D = st;  // D(r, c) = D[c * TLD + r]
         double xv[2] = {0.0, 0.0};
+        // fully unrolled so that acc[] and xv[] stay in registers (the pivot
+        // index is a compile-time constant in every step)
         if (TRANS == 0) {
-          for (int i = rows - 1; i >= 0; --i) {
+#pragma unroll
+          for (int i = TB - 1; i >= 0; --i) {
+            if (i >= rows) continue;
             const int hh = i >> 5, ln = i & 31;
             const double xi = __shfl_sync(0xffffffffu, acc[hh], ln) * srec[i];
             if (lane == ln) xv[hh] = xi;
@@ -343,7 +351,9 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
             if (lane + 32 < i) acc[1] -= D[i * TLD + lane + 32] * xi;
           }
         } else {
-          for (int i = 0; i < rows; ++i) {
+#pragma unroll
+          for (int i = 0; i < TB; ++i) {
+            if (i >= rows) continue;
             const int hh = i >> 5, ln = i & 31;
             const double xi = __shfl_sync(0xffffffffu, acc[hh], ln) * srec[i];
             if (lane == ln) xv[hh] = xi;
@@ -388,8 +398,8 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
     for (int m = 0; m < HMAXT; ++m) {
       if (m < nt && tg[m] >= u + CHAIN_NEAR) {
         const int k = chain_block<TRANS>(tg[m], nblk);
-        if (TRANS == 0) load_tile(tiles + m * TTILE, a.R, a.ldr, n, k, j);
-        else load_tile(tiles + m * TTILE, a.R, a.ldr, n, j, k);
+        if (TRANS == 0) load_tile(tiles + m * TTILE, a.R, a.ldr, n, k, j, tid, blockDim.x);
+        else load_tile(tiles + m * TTILE, a.R, a.ldr, n, j, k, tid, blockDim.x);
       }
     }
     cp_async_commit();

@@ -144,30 +144,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// All eight levels of 8 columns with one wait: the loads are issued back to
-// back, then one tcgen05.wait::ld; the empty asm statements after the wait
-// take the loaded registers as operands, so no use of them can be scheduled
-// before the wait.  Levels >= nlev (never written by the MMA) read as 0.
-__device__ __forceinline__ void tmem_levels_all(uint32_t cbase, int nlev, uint32_t (&r)[MAXD][8]) {
-#pragma unroll
-  for (int l = 0; l < MAXD; ++l) {
-    if (l < nlev) {
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]), "=r"(r[l][5]),
-                     "=r"(r[l][6]), "=r"(r[l][7])
-                   : "r"(cbase + (uint32_t)(l * BN)));
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) r[l][i] = 0u;
-    }
-  }
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int l = 0; l < MAXD; ++l)
-    asm volatile("" : "+r"(r[l][0]), "+r"(r[l][1]), "+r"(r[l][2]), "+r"(r[l][3]), "+r"(r[l][4]), "+r"(r[l][5]),
-                 "+r"(r[l][6]), "+r"(r[l][7]));
-}
-
 // Levels l0 .. l0+3 of 8 columns (levels >= nlev read as 0) combined exactly,
 // L_l0 2^(3 BETA) + L_(l0+1) 2^(2 BETA) + L_(l0+2) 2^BETA + L_(l0+3), and
 // added to acc[0..7].  (Ten warps leave 168 registers a thread, which the
@@ -246,6 +222,11 @@ struct OzArgs {
   long long ldc, M, N;
   int mode;           // 0: C = AB, 1: C -= AB
   unsigned* err;
+  // optional (single-chunk tiles): per column j >= key_c0 of the result, the
+  // largest exponent key (0 for zero, biased exponent + 1 otherwise) over
+  // rows i >= key_r0 is folded into ekey[j - key_c0] with atomicMax
+  int* ekey;
+  long long key_r0, key_c0;
 };
 
 struct __align__(8) OzBars {
@@ -386,70 +367,96 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     unsigned cglob = 0;
     bool alive = true;
     if (nchunks == 1) {
-      // One 512-deep chunk per tile (K <= 512: the QR trailing update).  Per
-      // group of 8 columns all levels are loaded with one wait; C and the
-      // column exponents of the next group are loaded while this group is
-      // combined; the accumulators are released as soon as the last group's
-      // levels are in registers, so the next tile's MMAs overlap the rest.
+      // One 512-deep chunk per tile (K <= 512: the QR trailing update).  The
+      // accumulators are drained first, eight levels of four columns per
+      // wait, each element kept as H 2^28 + L (H = L_0..3 combined plus the
+      // high part of L_4..7, 0 <= L < 2^28: 96 bits in three registers); the
+      // TMEM is released at once, and the rounding to FP64 and the C update
+      // run while the next tile's MMAs fill the accumulators again.
       for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
         const int mt = t % g.mtiles, nt = t / g.mtiles;
         const long long gi = (long long)mt * BM + row;
         const bool rin = gi < g.M;
-        const int ei = rin ? __ldg(g.ea + gi) : 0;
-        double cn[8];
-        int ebn[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const long long gj = (long long)nt * BN + col0 + i;
-          const bool in = rin && gj < g.N;
-          ebn[i] = gj < g.N ? __ldg(g.eb + gj) : 0;
-          cn[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
-        }
+        if (g.mode != 0 && rin)  // C is read in the final update: start bringing it into L2 now
+#pragma unroll 4
+          for (int j = 0; j < EPI_COLS; ++j) {
+            const long long gj = (long long)nt * BN + col0 + j;
+            if (gj < g.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(g.C + gi + gj * g.ldc));
+          }
         const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, cglob & 1, g.err, 9));
         tc_fence_after();
         if (!ok) {
           alive = false;
           break;
         }
-#pragma unroll 1
-        for (int grp = 0; grp < EPI_COLS / 8; ++grp) {
-          uint32_t r[MAXD][8];
-          tmem_levels_all(tmem + tlane + (uint32_t)(col0 + grp * 8), nlev, r);
-          if (grp == EPI_COLS / 8 - 1) {  // every level of this warp's columns is in registers
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bars->acc_empty);
-            ++cglob;
-          }
-          double cc[8];
-          int eb[8];
+        long long H[EPI_COLS];
+        unsigned L[EPI_COLS];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            cc[i] = cn[i];
-            eb[i] = ebn[i];
-          }
-          if (grp + 1 < EPI_COLS / 8) {
+        for (int grp = 0; grp < EPI_COLS / 4; ++grp) {
+          uint32_t r[MAXD][4];
+          const uint32_t cb = tmem + tlane + (uint32_t)(col0 + grp * 4);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const long long gj = (long long)nt * BN + col0 + (grp + 1) * 8 + i;
-              const bool in = rin && gj < g.N;
-              ebn[i] = gj < g.N ? __ldg(g.eb + gj) : 0;
-              cn[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
+          for (int l = 0; l < MAXD; ++l) {
+            if (l < nlev) {
+              asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                           : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3])
+                           : "r"(cb + (uint32_t)(l * BN)));
+            } else {
+              r[l][0] = r[l][1] = r[l][2] = r[l][3] = 0u;
             }
           }
-          if (rin) {
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              long long hi = 0, lo = 0;
+          for (int l = 0; l < MAXD; ++l)  // no use of the loaded registers before the wait
+            asm volatile("" : "+r"(r[l][0]), "+r"(r[l][1]), "+r"(r[l][2]), "+r"(r[l][3]));
 #pragma unroll
-              for (int l = 0; l < 4; ++l) hi = (hi << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
+          for (int i = 0; i < 4; ++i) {
+            long long hi = 0, lo = 0;
 #pragma unroll
-              for (int l = 4; l < MAXD; ++l) lo = (lo << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
-              const long long gj = (long long)nt * BN + col0 + grp * 8 + i;
-              if (gj < g.N) {
-                const double val = fix_to_double(hi, lo, ei + eb[i] - 9 * BETA);
-                g.C[gi + gj * g.ldc] = g.mode == 0 ? val : cc[i] - val;
-              }
+            for (int l = 0; l < 4; ++l) hi = (hi << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
+#pragma unroll
+            for (int l = 4; l < MAXD; ++l) lo = (lo << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
+            H[grp * 4 + i] = hi + (lo >> 28);
+            L[grp * 4 + i] = (unsigned)(lo & 0xFFFFFFFll);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->acc_empty);
+        ++cglob;
+        const int ei = rin ? __ldg(g.ea + gi) : 0;
+#pragma unroll
+        for (int j0 = 0; j0 < EPI_COLS; j0 += EPI_GRP) {
+          double cv[EPI_GRP];
+          int eb[EPI_GRP];
+          unsigned key[EPI_GRP];
+#pragma unroll
+          for (int i = 0; i < EPI_GRP; ++i) {
+            const long long gj = (long long)nt * BN + col0 + j0 + i;
+            const bool in = rin && gj < g.N;
+            eb[i] = gj < g.N ? __ldg(g.eb + gj) : 0;
+            cv[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
+            key[i] = 0u;
+          }
+#pragma unroll
+          for (int i = 0; i < EPI_GRP; ++i) {
+            const long long gj = (long long)nt * BN + col0 + j0 + i;
+            if (rin && gj < g.N) {
+              // value = 2^(e+f-9 BETA) (H 2^(4 BETA) + L), one rounding to FP64
+              const double val = fix_to_double(H[j0 + i], (long long)L[j0 + i], ei + eb[i] - 9 * BETA);
+              const double out = g.mode == 0 ? val : cv[i] - val;
+              g.C[gi + gj * g.ldc] = out;
+              const unsigned long long bits = (unsigned long long)__double_as_longlong(out);
+              if (gi >= g.key_r0 && (bits << 1) != 0ull) key[i] = (unsigned)((bits >> 52) & 0x7FF) + 1u;
+            }
+          }
+          if (g.ekey) {  // warp-uniform: fold the column maxima of the next trailing matrix
+#pragma unroll
+            for (int i = 0; i < EPI_GRP; ++i) {
+              const unsigned kmax = __reduce_max_sync(0xffffffffu, key[i]);
+              const long long gj = (long long)nt * BN + col0 + j0 + i;
+              if (lane == i && kmax != 0u && gj >= g.key_c0 && gj < g.N)
+                atomicMax(g.ekey + (gj - g.key_c0), (int)kmax);
             }
           }
         }
@@ -678,6 +685,15 @@ __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict_
 }
 
 
+// e[i] from an exponent key (0: zero row, else largest biased exponent + 1),
+// the same value k_rowexp computes from the row itself.
+__global__ void k_keys_to_exp(const int* __restrict__ keys, long long R, int* __restrict__ e) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= R) return;
+  const int k = keys[i];
+  e[i] = k == 0 ? 0 : (k == 1 ? -1022 : k - 1 - 1022);
+}
+
 size_t oz_smem_bytes() { return (size_t)ASTAGES * ATILE + 2 * MAXD * BTILE + sizeof(OzBars) + 1024; }
 
 }  // namespace
@@ -710,6 +726,26 @@ rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, 
                                 int tile_rows, int* e, uint16_t* out, cudaStream_t st) {
   return slice(AccStrided{base, si, sk}, R, K, ndig, tile_rows, e, out, st);
 }
+
+// Digits of a strided operand whose row exponents were gathered while it was
+// written (exponent keys of k_oz_gemm): keys -> e, then one digit pass.
+rfm_status rfm_oz_slice_strided_keys(const double* base, long long si, long long sk, long long R, long long K,
+                                     int ndig, int tile_rows, const int* keys, int* e, uint16_t* out,
+                                     cudaStream_t st) {
+  ProfScope ps(PF_OZ_SLICE, st);
+  k_keys_to_exp<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(keys, R, e);
+  RFM_CHECK_LAUNCH();
+  const long long rt = (R + tile_rows - 1) / tile_rows, kt = (K + 63) / 64;
+  const long long total = rt * tile_rows * kt * 8;
+  const int g2 = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+  const AccStrided X{base, si, sk};
+  if (tile_rows == BM)
+    k_digits<AccStrided, BM><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
+  else
+    k_digits<AccStrided, BN><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
+  RFM_CHECK_LAUNCH();
+  return RFM_OK;
+}
 rfm_status rfm_oz_slice_house_vt(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
                                  int* e, uint16_t* out, cudaStream_t st) {
   return slice(AccHouseVt{A, lda, j0}, nb, K, ndig, BM, e, out, st);
@@ -726,7 +762,7 @@ rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* ro
 
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
-                       unsigned* err, cudaStream_t st) {
+                       unsigned* err, cudaStream_t st, int* ekey, long long key_r0, long long key_c0) {
   if (pA < 1 || pB < 1 || pA > MAXD || pB > MAXD || Lmax < 2 || Lmax - 1 > 8) {
     rfm_set_error("oz_gemm: bad digit counts");
     return RFM_EINVAL;
@@ -738,6 +774,11 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
   a.ntiles = (int)((N + BN - 1) / BN);
   a.ktiles = (int)((K + BK - 1) / BK);
   a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
+  a.ekey = ekey; a.key_r0 = key_r0; a.key_c0 = key_c0;
+  if (ekey && K > (long long)KCHUNK * BK) {
+    rfm_set_error("oz_gemm: exponent keys need K <= 512");
+    return RFM_EINVAL;
+  }
   if (a.ktiles == 0) return RFM_OK;
   ProfScope ps(PF_OZ_GEMM, st);
   {

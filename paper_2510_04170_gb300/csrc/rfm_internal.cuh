@@ -181,7 +181,13 @@ rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* ro
                                int W, int ndig, int* e, uint16_t* out, cudaStream_t st);
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
-                       unsigned* err, cudaStream_t st);
+                       unsigned* err, cudaStream_t st, int* ekey = nullptr, long long key_r0 = 0,
+                       long long key_c0 = 0);
+rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, long long R, long long K, int ndig,
+                                int tile_rows, int* e, uint16_t* out, cudaStream_t st);
+rfm_status rfm_oz_slice_strided_keys(const double* base, long long si, long long sk, long long R, long long K,
+                                     int ndig, int tile_rows, const int* keys, int* e, uint16_t* out,
+                                     cudaStream_t st);
 long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows);
 rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda,
                                    cudaStream_t st, double* scratch, long long scratch_len,
@@ -232,8 +238,10 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
 // SYNC_WAITLIM holds the limit: 0 the default of 2^22 polls (well under a
 // second of sleeping), a positive count that many polls, a negative value
 // "give up at once" (a host-side test setting, rfm_set_wait_limit).
+// `pause_ns` > 0 sleeps that long between polls from the start (many waiters
+// on one line leave the L2 slice free for the write they wait for).
 __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want,
-                                          unsigned int* err) {
+                                          unsigned int* err, unsigned int pause_ns = 0) {
   const int lim = (int)__ldcg(err + (SYNC_WAITLIM - SYNC_ERR));
   if (lim < 0) {
     atomicExch(err, 1u);
@@ -246,7 +254,8 @@ __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int
       atomicExch(err, 1u);
       return false;
     }
-    if (spins > (1u << 16)) __nanosleep(128);
+    if (pause_ns) __nanosleep(pause_ns);
+    else if (spins > (1u << 16)) __nanosleep(128);
   }
   return true;
 }

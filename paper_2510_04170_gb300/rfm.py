@@ -23,7 +23,7 @@ EXPORTS = ["rfm_default_opts", "rfm_last_error", "rfm_problem_create", "rfm_prob
            "rfm_feature_gram", "rfm_function_basis", "rfm_basis_combine", "rfm_warmstart_create",
            "rfm_warmstart_destroy", "rfm_warmstart_rank", "rfm_warmstart_network", "rfm_warmstart_train",
            "rfm_warmstart_predict", "rfm_batch_create", "rfm_batch_destroy", "rfm_batch_size", "rfm_batch_problem",
-           "rfm_batch_solve", "rfm_autotune_qr", "rfm_set_wait_limit"]
+           "rfm_batch_solve", "rfm_autotune_qr", "rfm_set_wait_limit", "rfm_set_rhs"]
 
 
 class RfmError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path=LIB_PATH):
         "rfm_problem_destroy": (I, [P]),
         "rfm_problem_sizes": (I, [P] + [ctypes.POINTER(I64)] * 7),
         "rfm_set_wait_limit": (I, [P, I64]),
+        "rfm_set_rhs": (I, [P, VP]),
         "rfm_get_features": (I, [P, VP]),
         "rfm_get_points": (I, [P, VP]),
         "rfm_assemble": (I, [P, VP, D, VP, VP]),
@@ -244,6 +245,9 @@ class Problem:
 
     def rfm_set_wait_limit(self, polls):
         _check(load().rfm_set_wait_limit(self._h, polls))
+
+    def rfm_set_rhs(self, rhs):
+        _check(load().rfm_set_rhs(self._h, _ptr(rhs)))
 
     def rfm_sketch(self, kind, s, kJ, copy_out=True):
         B = self._dev(self.n, s) if copy_out else None

@@ -281,6 +281,28 @@ def test_invalid_descriptions_are_rejected():
     with pytest.raises(rfm.RfmError):
         rfm.Problem(W.with_(W.small_3d(), fields=2))   # two fields only for Gray-Scott
     with pytest.raises(rfm.RfmError):
-        rfm.Problem(W.small_2d(pde_kind=5))            # kinds 4-6 are three-dimensional
+        rfm.Problem(W.small_2d(pde_kind=5))            # kinds 4-7 are three-dimensional
     with pytest.raises(rfm.RfmError):
-        rfm.Problem(W.small_3d(pde_kind=7, pde_params=[0.0]))
+        rfm.Problem(W.small_3d(pde_kind=8, pde_params=[0.0]))
+
+
+def test_set_rhs_replaces_source_and_boundary_data():
+    """rfm_set_rhs: the residual with data f + delta (interior) and g + delta
+    (boundary) is the manufactured-data residual minus lambda * delta; the
+    interface rows keep zero data."""
+    desc = CASES["3d_ragged"]
+    op = OProblem(desc)
+    gp = G().Problem(desc)
+    c = W.random_coeffs(op.n, seed=3, scale=0.5)
+    F, lam = gp.rfm_assemble(dev(c))
+    Fo = asm.residual(op, c)
+    rhs0 = np.zeros(op.m)
+    rhs0[: op.m_int] = op.source(op.rx[: op.m_int], 0)
+    rhs0[op.m_int + op.m_iface:] = op.boundary_data(op.rx[op.m_int + op.m_iface:], 0)
+    delta = np.random.default_rng(21).standard_normal(op.m)
+    gp.rfm_set_rhs(dev(rhs0 + delta))
+    Fr, _ = gp.rfm_residual(dev(c))
+    lamo = host(lam)
+    expect = lamo * Fo - lamo * delta
+    expect[op.m_int:op.m_int + op.m_iface] = lamo[op.m_int:op.m_int + op.m_iface] * Fo[op.m_int:op.m_int + op.m_iface]
+    assert np.max(np.abs(host(Fr) - expect)) <= 1e-12 * max(1.0, np.abs(expect).max())
