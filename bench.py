@@ -571,6 +571,41 @@ def forms_record(args, wl, rfm, line, info):
     import torch
     from paper_2510_04170_gb300 import warmstart
     out = {}
+    # -- mixed precision: the headline instance in plain FP64
+    ph = info
+    est = (8.5 * ph["t_qr"] + 3.0 * ph["t_sketch"] + (ph["t_total"] - ph["t_qr"] - ph["t_sketch"])) / 1e3
+    elapsed = time.time() - T_START
+    mixed = {"solves_per_s": line["value"] if line["value"] is not None else line.get("value_ungated"),
+             "rel_l2_vs_oracle": line["accuracy"].get("rel_l2_vs_oracle")}
+    rec = {"mixed_solves_per_s": mixed["solves_per_s"], "mixed_rel_l2_vs_oracle": mixed["rel_l2_vs_oracle"],
+           "plain_projected_s": est}
+    if args.forms == "on" or elapsed + est <= args.budget:
+        import torch as _t
+        stream = _t.cuda.Stream()
+        with _t.cuda.stream(stream):
+            gp = rfm.Problem(wl["desc"], stream=stream)
+        opts0 = dict(wl["opts"], precision=0)
+        a = _t.cuda.Event(enable_timing=True)
+        b = _t.cuda.Event(enable_timing=True)
+        with _t.cuda.stream(stream):
+            a.record(stream)
+            c, inf0 = gp.rfm_ipn_solve(opts0)
+            b.record(stream)
+        b.synchronize()
+        t_plain = a.elapsed_time(b) / 1e3
+        X = W.eval_grid(wl["desc"])
+        u = gp.rfm_eval(c, _t.as_tensor(X, device="cuda")).cpu().numpy()
+        ref = stored_oracle_solve(args, wl)
+        rec.update({"plain_solves_per_s": 1.0 / t_plain, "plain_status": STATUS[inf0["status"]],
+                    "plain_counts": [inf0["outer_iters"], inf0["n_jac"], inf0["lsqr_iters_total"]],
+                    "gain": mixed["solves_per_s"] * t_plain if mixed["solves_per_s"] else None})
+        if ref is not None:
+            rec["plain_rel_l2_vs_oracle"] = float(np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"]))
+        gp.close()
+    else:
+        rec["plain"] = (f"skipped: {elapsed:.0f} s elapsed + {est:.0f} s projected exceeds the "
+                        f"{args.budget:.0f} s budget")
+    out["mixed_precision"] = rec
     # -- batching: the same instances on one stream vs eight (tensor-core QR)
     descs = [d for i, d in enumerate(W.config_c4_instances(64, seed=1)) if i % 3 != 2][:args.forms_instances]
     res = {}
@@ -622,41 +657,6 @@ def forms_record(args, wl, rfm, line, info):
         "n_jac_mean_warm": float(np.mean([i["n_jac"] for i in iw])),
         "rel_l2_warm_vs_zero_max": max(rel)}
     bz.close()
-    # -- mixed precision: the headline instance in plain FP64
-    ph = info
-    est = (8.5 * ph["t_qr"] + 3.0 * ph["t_sketch"] + (ph["t_total"] - ph["t_qr"] - ph["t_sketch"])) / 1e3
-    elapsed = time.time() - T_START
-    mixed = {"solves_per_s": line["value"] if line["value"] is not None else line.get("value_ungated"),
-             "rel_l2_vs_oracle": line["accuracy"].get("rel_l2_vs_oracle")}
-    rec = {"mixed_solves_per_s": mixed["solves_per_s"], "mixed_rel_l2_vs_oracle": mixed["rel_l2_vs_oracle"],
-           "plain_projected_s": est}
-    if args.forms == "on" or elapsed + est <= args.budget:
-        import torch as _t
-        stream = _t.cuda.Stream()
-        with _t.cuda.stream(stream):
-            gp = rfm.Problem(wl["desc"], stream=stream)
-        opts0 = dict(wl["opts"], precision=0)
-        a = _t.cuda.Event(enable_timing=True)
-        b = _t.cuda.Event(enable_timing=True)
-        with _t.cuda.stream(stream):
-            a.record(stream)
-            c, inf0 = gp.rfm_ipn_solve(opts0)
-            b.record(stream)
-        b.synchronize()
-        t_plain = a.elapsed_time(b) / 1e3
-        X = W.eval_grid(wl["desc"])
-        u = gp.rfm_eval(c, _t.as_tensor(X, device="cuda")).cpu().numpy()
-        ref = stored_oracle_solve(args, wl)
-        rec.update({"plain_solves_per_s": 1.0 / t_plain, "plain_status": STATUS[inf0["status"]],
-                    "plain_counts": [inf0["outer_iters"], inf0["n_jac"], inf0["lsqr_iters_total"]],
-                    "gain": mixed["solves_per_s"] * t_plain if mixed["solves_per_s"] else None})
-        if ref is not None:
-            rec["plain_rel_l2_vs_oracle"] = float(np.linalg.norm(u - ref["u"]) / np.linalg.norm(ref["u"]))
-        gp.close()
-    else:
-        rec["plain"] = (f"skipped: {elapsed:.0f} s elapsed + {est:.0f} s projected exceeds the "
-                        f"{args.budget:.0f} s budget")
-    out["mixed_precision"] = rec
     return out
 
 
@@ -803,7 +803,7 @@ def main():
                     help="c4/c5: use only this many instances (functional runs; the label says so)")
     ap.add_argument("--forms", default="auto", choices=["auto", "on", "off"],
                     help="c2: add the plain-vs-forms comparison (auto: the plain FP64 solve only within --budget)")
-    ap.add_argument("--budget", type=float, default=1500.0, help="wall-clock seconds for --forms auto")
+    ap.add_argument("--budget", type=float, default=1650.0, help="wall-clock seconds for --forms auto")
     ap.add_argument("--forms-instances", type=int, default=16)
     ap.add_argument("--forms-train", type=int, default=128)
     args = ap.parse_args()

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
 // once), and publishes each target's partial sum three steps before the
 // chain needs it.  All sums are in a fixed order, so results are
 // deterministic.  Waits are bounded (wait_flag).
-constexpr int TLD = TB + 1;            // leading dimension of a shared-memory tile (doubles)
+constexpr int TLD = TB + 2;            // leading dimension of a shared-memory tile (doubles; 16-byte rows)
 constexpr int TTILE = TB * TLD;        // doubles per shared-memory tile
 constexpr int CHAIN_NEAR = 3;          // the chain applies distances 1 .. CHAIN_NEAR-1 itself
 constexpr int HMAXT = 4;               // targets per helper CTA
@@ -224,6 +224,11 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src) {
                "l"(src)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(double* dst, const double* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -233,12 +238,22 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // Entries outside the n x n triangle's index range are zero.
 __device__ __forceinline__ void load_tile(double* T, const double* __restrict__ R, long long ldr, int n, int a,
                                           int b, int first, int stride) {
-  for (int idx = first; idx < TB * TB; idx += stride) {
-    const int rr = idx & (TB - 1), cc = idx >> 6;
+  // pairs of rows: one 16-byte copy when both lie inside (R's leading
+  // dimension and row offsets are even, so the source is 16-byte aligned)
+  const bool even = (ldr & 1) == 0;
+  for (int idx = first; idx < TB * TB / 2; idx += stride) {
+    const int rr = (idx & (TB / 2 - 1)) * 2, cc = idx >> 5;
     const int gr = a * TB + rr, gc = b * TB + cc;
     double* dst = T + cc * TLD + rr;
-    if (gr < n && gc < n) cp_async8(dst, R + (size_t)gc * ldr + gr);
-    else *dst = 0.0;
+    const double* src = R + (size_t)gc * ldr + gr;
+    if (gc < n && gr + 1 < n && even) {
+      cp_async16(dst, src);
+    } else {
+      if (gc < n && gr < n) cp_async8(dst, src);
+      else dst[0] = 0.0;
+      if (gc < n && gr + 1 < n) cp_async8(dst + 1, src + 1);
+      else dst[1] = 0.0;
+    }
   }
 }
 
@@ -386,78 +401,110 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
   }
   if (nt == 0) return;
   const int tmax = tg[nt - 1];
-  double* tiles = csm;                   // [HMAXT] tiles
-  double* sred = csm + HMAXT * TTILE;    // [8][64]
-  double pa[HMAXT][2];                   // partial sums of rows lane, lane+32 (this warp's sources)
+  double* sred = csm;                    // [8][64]
+  __shared__ unsigned int seen_s;        // progress counter as last read
+  double pa[HMAXT][2];   // TRANS 0: partial sums of target rows lane, lane+32 over this warp's sources
+  double ptp[HMAXT][8];  // TRANS 1: partial sums of target rows w + 8 q over this lane's sources
 #pragma unroll
-  for (int m = 0; m < HMAXT; ++m) pa[m][0] = pa[m][1] = 0.0;
+  for (int m = 0; m < HMAXT; ++m) {
+    pa[m][0] = pa[m][1] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ptp[m][q] = 0.0;
+  }
+  unsigned int seen = 0;
+  const int lim = (int)__ldcg(a.err + (SYNC_WAITLIM - SYNC_ERR));
+  const unsigned int limit = lim == 0 ? (1u << 22) : (unsigned int)lim;
   for (int u = 0; u + CHAIN_NEAR <= tmax; ++u) {
     const int j = chain_block<TRANS>(u, nblk);
-    // tiles first (they do not depend on x), then wait for block u
-#pragma unroll
-    for (int m = 0; m < HMAXT; ++m) {
-      if (m < nt && tg[m] >= u + CHAIN_NEAR) {
-        const int k = chain_block<TRANS>(tg[m], nblk);
-        if (TRANS == 0) load_tile(tiles + m * TTILE, a.R, a.ldr, n, k, j, tid, blockDim.x);
-        else load_tile(tiles + m * TTILE, a.R, a.ldr, n, j, k, tid, blockDim.x);
-      }
-    }
-    cp_async_commit();
-    if (tid == 0) {
-      // the progress counter only grows: wait until block u is published
-      const unsigned int want = (unsigned int)(u + 1);
-      const int lim = (int)__ldcg(a.err + (SYNC_WAITLIM - SYNC_ERR));
-      const unsigned int limit = lim == 0 ? (1u << 22) : (unsigned int)lim;
-      unsigned int spins = 0;
-      while (ld_acquire(a.prog) < want) {
-        if (lim < 0 || ++spins > limit) {
-          atomicExch(a.err, 1u);
-          break;
-        }
-        if (spins > (1u << 16)) __nanosleep(128);
-      }
-    }
-    cp_async_wait0();
-    __syncthreads();
     const int c0 = j * TB;
-    double xv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int y = w + 8 * q;
-      xv[q] = c0 + y < n ? __ldcg(a.x + c0 + y) : 0.0;
-    }
+    // this step's tile entries into registers first (they do not depend on
+    // x): TRANS 0 rows lane, lane+32 of R(k, j), columns w + 8 q; TRANS 1
+    // rows w + 8 q of R(j, k) (columns of block k), read along j's rows
+    double tv[HMAXT][16];
 #pragma unroll
     for (int m = 0; m < HMAXT; ++m) {
-      if (!(m < nt && tg[m] >= u + CHAIN_NEAR)) continue;
-      const double* T = tiles + m * TTILE;
+      const bool live = m < nt && tg[m] >= u + CHAIN_NEAR;
+      const int k = live ? chain_block<TRANS>(tg[m], nblk) : 0;
+      const int r0 = k * TB;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int y = w + 8 * q;
-        if (TRANS == 0) {
-          pa[m][0] += T[y * TLD + lane] * xv[q];
-          pa[m][1] += T[y * TLD + lane + 32] * xv[q];
-        } else {
-          pa[m][0] += T[lane * TLD + y] * xv[q];
-          pa[m][1] += T[(lane + 32) * TLD + y] * xv[q];
+        if (TRANS == 0) {  // R(r0 + lane (+32), c0 + y)
+          const bool ok = live && c0 + y < n;
+          const double* col = a.R + (size_t)(c0 + y) * a.ldr + r0;
+          tv[m][2 * q] = ok && r0 + lane < n ? __ldg(col + lane) : 0.0;
+          tv[m][2 * q + 1] = ok && r0 + lane + 32 < n ? __ldg(col + lane + 32) : 0.0;
+        } else {           // R(c0 + lane (+32), r0 + y): target row y
+          const bool ok = live && r0 + y < n;
+          const double* col = a.R + (size_t)(r0 + y) * a.ldr + c0;
+          tv[m][2 * q] = ok ? __ldg(col + lane) : 0.0;
+          tv[m][2 * q + 1] = ok ? __ldg(col + lane + 32) : 0.0;
         }
       }
     }
-    __syncthreads();  // tiles are refilled next step
+    // block u published?  (the counter only grows; read it again only when needed)
+    if (seen < (unsigned int)(u + 1)) {
+      if (tid == 0) {
+        unsigned int v = ld_acquire(a.prog), spins = 0;
+        while (v < (unsigned int)(u + 1)) {
+          if (lim < 0 || ++spins > limit) {
+            atomicExch(a.err, 1u);
+            v = (unsigned int)(u + 1);
+            break;
+          }
+          if (spins > (1u << 16)) __nanosleep(128);
+          v = ld_acquire(a.prog);
+        }
+        seen_s = v;
+      }
+      __syncthreads();
+      seen = seen_s;
+    }
+    if (TRANS == 0) {
+      double xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int y = w + 8 * q;
+        xv[q] = c0 + y < n ? __ldcg(a.x + c0 + y) : 0.0;
+      }
+#pragma unroll
+      for (int m = 0; m < HMAXT; ++m)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          pa[m][0] += tv[m][2 * q] * xv[q];
+          pa[m][1] += tv[m][2 * q + 1] * xv[q];
+        }
+    } else {
+      const double z0 = __ldcg(a.x + c0 + lane), z1 = __ldcg(a.x + c0 + lane + 32);
+#pragma unroll
+      for (int m = 0; m < HMAXT; ++m)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ptp[m][q] += tv[m][2 * q] * z0 + tv[m][2 * q + 1] * z1;
+    }
     // a target whose last helper source this was: publish its partial sum
 #pragma unroll
     for (int m = 0; m < HMAXT; ++m) {
       if (!(m < nt && tg[m] == u + CHAIN_NEAR)) continue;
       const int k = chain_block<TRANS>(tg[m], nblk);
-      sred[w * TB + lane] = pa[m][0];
-      sred[w * TB + lane + 32] = pa[m][1];
-      __syncthreads();
-      if (w == 0) {
-        double* out = a.accbuf + (size_t)k * TB;
-        for (int hh = 0; hh < 2; ++hh) {
-          double sm = 0.0;
+      double* out = a.accbuf + (size_t)k * TB;
+      if (TRANS == 0) {
+        sred[w * TB + lane] = pa[m][0];
+        sred[w * TB + lane + 32] = pa[m][1];
+        __syncthreads();
+        if (w == 0) {
+          for (int hh = 0; hh < 2; ++hh) {
+            double sm = 0.0;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) sm += sred[q * TB + lane + 32 * hh];
-          out[lane + 32 * hh] = sm;
+            for (int q = 0; q < 8; ++q) sm += sred[q * TB + lane + 32 * hh];
+            out[lane + 32 * hh] = sm;
+          }
+          __threadfence();
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const double v = warp_sum(ptp[m][q]);
+          if (lane == 0) out[w + 8 * q] = v;
         }
         __threadfence();
       }
