@@ -57,7 +57,6 @@ constexpr int EPI_COLS = BN / (EPI_WARPS / 4);
 constexpr int EPI_GRP = 4;          // C elements loaded per round trip in the final update
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int KCHUNK = 8;           // k-tiles per exact chunk (8 * 64 = 512)
-constexpr int DRAIN_COLS = 2;       // columns per TMEM drain step (all eight levels, one wait)
 constexpr int BETA = 7;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up after 2 s
 
@@ -135,6 +134,38 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Levels l0 .. l0+3 of 8 columns (levels >= nlev read as 0) combined exactly,
+// L_l0 2^(3 BETA) + L_(l0+1) 2^(2 BETA) + L_(l0+2) 2^BETA + L_(l0+3), and
+// added to acc[0..7].  (Ten warps leave 168 registers a thread, which the
+// accumulators mostly fill, so one level is loaded per wait.)
+__device__ __forceinline__ void tmem_levels4(uint32_t cbase, int l0, int nlev, long long* acc) {
+  float v[8];
+  long long I[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (l0 + q < nlev) {  // warp-uniform
+      tmem_ld8(cbase + (uint32_t)((l0 + q) * BN), v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) I[i] = (q == 0 ? 0 : I[i] << BETA) + (long long)__float2int_rn(v[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) I[i] = q == 0 ? 0 : I[i] << BETA;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] += I[i];
+}
+
 // (ah 2^28 + al) 2^k rounded to the nearest double (ties to even) with integer
 // operations only: the 128-bit two's-complement sum, its leading bit, a 53-bit
 // mantissa with round and sticky bits, and the exponent field; ldexp of the
@@ -180,6 +211,7 @@ __device__ __forceinline__ double fix_to_double(long long ah, long long al, int 
 }
 
 // ---------------------------------------------------------------- GEMM kernel
+struct OzArgs;
 struct OzArgs {
   const uint16_t* A;  // digit tiles [pA][mtiles][ktiles][ATILE/2]
   const uint16_t* B;  // digit tiles [pB][ntiles][ktiles][BTILE/2]
@@ -191,12 +223,25 @@ struct OzArgs {
   long long ldc, M, N;
   int mode;           // 0: C = AB, 1: C -= AB
   unsigned* err;
-  // optional (single-chunk tiles): per column j >= key_c0 of the result, the
-  // largest exponent key (0 for zero, biased exponent + 1 otherwise) over
-  // rows i >= key_r0 is folded into ekey[j - key_c0] with atomicMax
+  // optional: per column j >= key_c0 of the result, the largest exponent key
+  // (0 for zero, biased exponent + 1 otherwise) over rows i >= key_r0 is
+  // folded into ekey[j - key_c0] with atomicMax (the next block's exponents)
   int* ekey;
   long long key_r0, key_c0;
 };
+
+// Folds a row's exponent keys of EPI_GRP consecutive columns (11-bit fields
+// of `packed`) into the column maxima of the next trailing block.  Called by
+// every lane of a warp (rows outside the matrix pass zeros).
+__device__ __forceinline__ void key_fold(unsigned long long packed, long long gi, long long gj0, const OzArgs& g) {
+  (void)gi;
+#pragma unroll
+  for (int i = 0; i < EPI_GRP; ++i) {
+    const unsigned kmax = __reduce_max_sync(0xffffffffu, (unsigned)(packed >> (11 * i)) & 0x7FFu);
+    const long long gj = gj0 + i;
+    if ((threadIdx.x & 31) == i && kmax != 0u && gj >= g.key_c0 && gj < g.N) atomicMax(g.ekey + (gj - g.key_c0), (int)kmax);
+  }
+}
 
 struct __align__(8) OzBars {
   uint64_t a_full[ASTAGES], a_empty[ASTAGES], b_full[2], b_empty[2], acc_full, acc_empty, fin;
@@ -335,29 +380,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
     unsigned cglob = 0;
     bool alive = true;
-    // Per tile: each 512-deep chunk's eight levels are drained from TMEM,
-    // DRAIN_COLS columns at a time with one wait for all eight loads, and folded
-    // into a running exact sum per element kept as AH 2^28 + AL (AH: levels
-    // 0-3 combined plus the high part of levels 4-7, 0 <= AL < 2^28; 96 bits
-    // in three registers); the accumulators are released after each chunk.
-    // The rounding to FP64 and the C update run after the tile's last
-    // release, while the MMAs of the next tile fill the accumulators again.
     for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
       const int mt = t % g.mtiles, nt = t / g.mtiles;
-      const long long gi = (long long)mt * BM + row;
-      const bool rin = gi < g.M;
-      if (g.mode != 0 && rin)  // C is read in the final update: start bringing it into L2 now
+      if (g.mode != 0) {  // C is read in the final update: start bringing it into L2 now
+        const long long gi = (long long)mt * BM + row;
+        if (gi < g.M)
 #pragma unroll 4
-        for (int j = 0; j < EPI_COLS; ++j) {
-          const long long gj = (long long)nt * BN + col0 + j;
-          if (gj < g.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(g.C + gi + gj * g.ldc));
-        }
-      long long AH[EPI_COLS];
-      unsigned AL[EPI_COLS];
+          for (int j = 0; j < EPI_COLS; ++j) {
+            const long long gj = (long long)nt * BN + col0 + j;
+            if (gj < g.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(g.C + gi + gj * g.ldc));
+          }
+      }
+      long long ai[EPI_COLS];  // levels 0-3, in units of level 3
+      long long al[EPI_COLS];  // levels 4-7, in units of level 7
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) {
-        AH[j] = 0;
-        AL[j] = 0u;
+        ai[j] = 0;
+        al[j] = 0;
       }
       for (int c = 0; c < nchunks; ++c) {
         const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, cglob & 1, g.err, 9));
@@ -367,38 +406,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
           break;
         }
 #pragma unroll
-        for (int grp = 0; grp < EPI_COLS / DRAIN_COLS; ++grp) {
-          uint32_t r[MAXD][DRAIN_COLS];
-          const uint32_t cb = tmem + tlane + (uint32_t)(col0 + grp * DRAIN_COLS);
-#pragma unroll
-          for (int l = 0; l < MAXD; ++l) {
-            if (l < nlev) {  // warp-uniform
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-                           : "=r"(r[l][0]), "=r"(r[l][1])
-                           : "r"(cb + (uint32_t)(l * BN)));
-            } else {  // never written by the MMA
-              r[l][0] = r[l][1] = 0u;
-            }
-          }
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int l = 0; l < MAXD; ++l)  // no use of the loaded registers before the wait
-            asm volatile("" : "+r"(r[l][0]), "+r"(r[l][1]));
-#pragma unroll
-          for (int i = 0; i < DRAIN_COLS; ++i) {
-            // levels 0-3 (exact integers below 2^24) and 4-7 (integers below
-            // 2^31; their FP32 sums may round above 2^24, far below the
-            // result's last bit), each combined exactly in int64
-            long long hi = 0, lo = 0;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) hi = (hi << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
-#pragma unroll
-            for (int l = 4; l < MAXD; ++l) lo = (lo << BETA) + (long long)__float2int_rn(__uint_as_float(r[l][i]));
-            const int j = grp * DRAIN_COLS + i;
-            const unsigned sl = AL[j] + (unsigned)(lo & 0xFFFFFFFll);  // < 2^29
-            AH[j] += hi + (lo >> 28) + (long long)(sl >> 28);
-            AL[j] = sl & 0xFFFFFFFu;
-          }
+        for (int grp = 0; grp < EPI_COLS / 8; ++grp) {
+          const uint32_t cbase = tmem + tlane + (uint32_t)(col0 + grp * 8);
+          // leading levels: exact integers below 2^24 (32-bit conversions),
+          // combined exactly in int64
+          tmem_levels4(cbase, 0, nlev, ai + grp * 8);
+          // remaining levels, combined the same way in int64 (their FP32
+          // accumulators may exceed 2^24 and round there, far below the
+          // result's last bit; the values stay integers below 2^31)
+          if (nlev > 4) tmem_levels4(cbase, 4, nlev, al + grp * 8);
         }
         tc_fence_before();
         __syncwarp();
@@ -406,43 +422,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
         ++cglob;
       }
       if (!alive) break;
-      const int ei = rin ? __ldg(g.ea + gi) : 0;
+      const long long gi = (long long)mt * BM + row;
+      const bool rin = gi < g.M;
+      const int ei = rin ? g.ea[gi] : 0;
       // EPI_GRP columns at a time: their exponents and (mode 1) C values are
       // loaded together, so one memory round trip serves EPI_GRP elements
 #pragma unroll
       for (int j0 = 0; j0 < EPI_COLS; j0 += EPI_GRP) {
         double cv[EPI_GRP];
         int eb[EPI_GRP];
-        unsigned key[EPI_GRP];
 #pragma unroll
         for (int i = 0; i < EPI_GRP; ++i) {
           const long long gj = (long long)nt * BN + col0 + j0 + i;
           const bool in = rin && gj < g.N;
-          eb[i] = gj < g.N ? __ldg(g.eb + gj) : 0;
+          eb[i] = in ? __ldg(g.eb + gj) : 0;
           cv[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
-          key[i] = 0u;
         }
+        unsigned long long key = 0ull;  // this row's exponent keys of the EPI_GRP columns, 11 bits each
 #pragma unroll
         for (int i = 0; i < EPI_GRP; ++i) {
           const long long gj = (long long)nt * BN + col0 + j0 + i;
           if (rin && gj < g.N) {
-            // value = 2^(e+f-9 BETA) (AH 2^(4 BETA) + AL), one rounding to FP64
-            const double val = fix_to_double(AH[j0 + i], (long long)AL[j0 + i], ei + eb[i] - 9 * BETA);
+            // value = 2^(e+f-9 BETA) (ai 2^(4 BETA) + al), one rounding to FP64
+            const double val = fix_to_double(ai[j0 + i], al[j0 + i], ei + eb[i] - 9 * BETA);
             const double out = g.mode == 0 ? val : cv[i] - val;
             g.C[gi + gj * g.ldc] = out;
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(out);
-            if (gi >= g.key_r0 && (bits << 1) != 0ull) key[i] = (unsigned)((bits >> 52) & 0x7FF) + 1u;
+            if (g.ekey && gi >= g.key_r0) {
+              const unsigned long long bits = (unsigned long long)__double_as_longlong(out);
+              const unsigned e = (bits << 1) != 0ull ? (unsigned)((bits >> 52) & 0x7FF) + 1u : 0u;
+              key |= (unsigned long long)e << (11 * i);
+            }
           }
         }
-        if (g.ekey) {  // warp-uniform: fold the column maxima of the next trailing matrix
-#pragma unroll
-          for (int i = 0; i < EPI_GRP; ++i) {
-            const unsigned kmax = __reduce_max_sync(0xffffffffu, key[i]);
-            const long long gj = (long long)nt * BN + col0 + j0 + i;
-            if (lane == i && kmax != 0u && gj >= g.key_c0 && gj < g.N)
-              atomicMax(g.ekey + (gj - g.key_c0), (int)kmax);
-          }
-        }
+        if (g.ekey) key_fold(key, gi, (long long)nt * BN + col0 + j0, g);  // warp-uniform
       }
     }
   }
@@ -688,10 +700,6 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
   a.ktiles = (int)((K + BK - 1) / BK);
   a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
   a.ekey = ekey; a.key_r0 = key_r0; a.key_c0 = key_c0;
-  if (ekey && K > (long long)KCHUNK * BK) {
-    rfm_set_error("oz_gemm: exponent keys need K <= 512");
-    return RFM_EINVAL;
-  }
   if (a.ktiles == 0) return RFM_OK;
   ProfScope ps(PF_OZ_GEMM, st);
   {
