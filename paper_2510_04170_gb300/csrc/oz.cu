@@ -211,7 +211,6 @@ __device__ __forceinline__ double fix_to_double(long long ah, long long al, int 
 }
 
 // ---------------------------------------------------------------- GEMM kernel
-struct OzArgs;
 struct OzArgs {
   const uint16_t* A;  // digit tiles [pA][mtiles][ktiles][ATILE/2]
   const uint16_t* B;  // digit tiles [pB][ntiles][ktiles][BTILE/2]
@@ -223,25 +222,7 @@ struct OzArgs {
   long long ldc, M, N;
   int mode;           // 0: C = AB, 1: C -= AB
   unsigned* err;
-  // optional: per column j >= key_c0 of the result, the largest exponent key
-  // (0 for zero, biased exponent + 1 otherwise) over rows i >= key_r0 is
-  // folded into ekey[j - key_c0] with atomicMax (the next block's exponents)
-  int* ekey;
-  long long key_r0, key_c0;
 };
-
-// Folds a row's exponent keys of EPI_GRP consecutive columns (11-bit fields
-// of `packed`) into the column maxima of the next trailing block.  Called by
-// every lane of a warp (rows outside the matrix pass zeros).
-__device__ __forceinline__ void key_fold(unsigned long long packed, long long gi, long long gj0, const OzArgs& g) {
-  (void)gi;
-#pragma unroll
-  for (int i = 0; i < EPI_GRP; ++i) {
-    const unsigned kmax = __reduce_max_sync(0xffffffffu, (unsigned)(packed >> (11 * i)) & 0x7FFu);
-    const long long gj = gj0 + i;
-    if ((threadIdx.x & 31) == i && kmax != 0u && gj >= g.key_c0 && gj < g.N) atomicMax(g.ekey + (gj - g.key_c0), (int)kmax);
-  }
-}
 
 struct __align__(8) OzBars {
   uint64_t a_full[ASTAGES], a_empty[ASTAGES], b_full[2], b_empty[2], acc_full, acc_empty, fin;
@@ -423,38 +404,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
       }
       if (!alive) break;
       const long long gi = (long long)mt * BM + row;
-      const bool rin = gi < g.M;
-      const int ei = rin ? g.ea[gi] : 0;
-      // EPI_GRP columns at a time: their exponents and (mode 1) C values are
-      // loaded together, so one memory round trip serves EPI_GRP elements
+      if (gi < g.M) {
+        const int ei = g.ea[gi];
+        // EPI_GRP columns at a time: their exponents and (mode 1) C values are
+        // loaded together, so one memory round trip serves EPI_GRP elements
 #pragma unroll
-      for (int j0 = 0; j0 < EPI_COLS; j0 += EPI_GRP) {
-        double cv[EPI_GRP];
-        int eb[EPI_GRP];
+        for (int j0 = 0; j0 < EPI_COLS; j0 += EPI_GRP) {
+          double cv[EPI_GRP];
+          int eb[EPI_GRP];
 #pragma unroll
-        for (int i = 0; i < EPI_GRP; ++i) {
-          const long long gj = (long long)nt * BN + col0 + j0 + i;
-          const bool in = rin && gj < g.N;
-          eb[i] = in ? __ldg(g.eb + gj) : 0;
-          cv[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
-        }
-        unsigned long long key = 0ull;  // this row's exponent keys of the EPI_GRP columns, 11 bits each
+          for (int i = 0; i < EPI_GRP; ++i) {
+            const long long gj = (long long)nt * BN + col0 + j0 + i;
+            const bool in = gj < g.N;
+            eb[i] = in ? __ldg(g.eb + gj) : 0;
+            cv[i] = (in && g.mode != 0) ? __ldcg(g.C + gi + gj * g.ldc) : 0.0;
+          }
 #pragma unroll
-        for (int i = 0; i < EPI_GRP; ++i) {
-          const long long gj = (long long)nt * BN + col0 + j0 + i;
-          if (rin && gj < g.N) {
-            // value = 2^(e+f-9 BETA) (ai 2^(4 BETA) + al), one rounding to FP64
-            const double val = fix_to_double(ai[j0 + i], al[j0 + i], ei + eb[i] - 9 * BETA);
-            const double out = g.mode == 0 ? val : cv[i] - val;
-            g.C[gi + gj * g.ldc] = out;
-            if (g.ekey && gi >= g.key_r0) {
-              const unsigned long long bits = (unsigned long long)__double_as_longlong(out);
-              const unsigned e = (bits << 1) != 0ull ? (unsigned)((bits >> 52) & 0x7FF) + 1u : 0u;
-              key |= (unsigned long long)e << (11 * i);
+          for (int i = 0; i < EPI_GRP; ++i) {
+            const long long gj = (long long)nt * BN + col0 + j0 + i;
+            if (gj < g.N) {
+              // value = 2^(e+f-9 BETA) (ai 2^(4 BETA) + al), one rounding to FP64
+              const double val = fix_to_double(ai[j0 + i], al[j0 + i], ei + eb[i] - 9 * BETA);
+              g.C[gi + gj * g.ldc] = g.mode == 0 ? val : cv[i] - val;
             }
           }
         }
-        if (g.ekey) key_fold(key, gi, (long long)nt * BN + col0 + j0, g);  // warp-uniform
       }
     }
   }
@@ -610,15 +584,6 @@ __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict_
 }
 
 
-// e[i] from an exponent key (0: zero row, else largest biased exponent + 1),
-// the same value k_rowexp computes from the row itself.
-__global__ void k_keys_to_exp(const int* __restrict__ keys, long long R, int* __restrict__ e) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= R) return;
-  const int k = keys[i];
-  e[i] = k == 0 ? 0 : (k == 1 ? -1022 : k - 1 - 1022);
-}
-
 size_t oz_smem_bytes() { return (size_t)ASTAGES * ATILE + 2 * MAXD * BTILE + sizeof(OzBars) + 1024; }
 
 }  // namespace
@@ -651,26 +616,6 @@ rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, 
                                 int tile_rows, int* e, uint16_t* out, cudaStream_t st) {
   return slice(AccStrided{base, si, sk}, R, K, ndig, tile_rows, e, out, st);
 }
-
-// Digits of a strided operand whose row exponents were gathered while it was
-// written (exponent keys of k_oz_gemm): keys -> e, then one digit pass.
-rfm_status rfm_oz_slice_strided_keys(const double* base, long long si, long long sk, long long R, long long K,
-                                     int ndig, int tile_rows, const int* keys, int* e, uint16_t* out,
-                                     cudaStream_t st) {
-  ProfScope ps(PF_OZ_SLICE, st);
-  k_keys_to_exp<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(keys, R, e);
-  RFM_CHECK_LAUNCH();
-  const long long rt = (R + tile_rows - 1) / tile_rows, kt = (K + 63) / 64;
-  const long long total = rt * tile_rows * kt * 8;
-  const int g2 = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
-  const AccStrided X{base, si, sk};
-  if (tile_rows == BM)
-    k_digits<AccStrided, BM><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
-  else
-    k_digits<AccStrided, BN><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
-  RFM_CHECK_LAUNCH();
-  return RFM_OK;
-}
 rfm_status rfm_oz_slice_house_vt(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
                                  int* e, uint16_t* out, cudaStream_t st) {
   return slice(AccHouseVt{A, lda, j0}, nb, K, ndig, BM, e, out, st);
@@ -687,7 +632,7 @@ rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* ro
 
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
-                       unsigned* err, cudaStream_t st, int* ekey, long long key_r0, long long key_c0) {
+                       unsigned* err, cudaStream_t st) {
   if (pA < 1 || pB < 1 || pA > MAXD || pB > MAXD || Lmax < 2 || Lmax - 1 > 8) {
     rfm_set_error("oz_gemm: bad digit counts");
     return RFM_EINVAL;
@@ -699,7 +644,6 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
   a.ntiles = (int)((N + BN - 1) / BN);
   a.ktiles = (int)((K + BK - 1) / BK);
   a.ea = ea; a.eb = eb; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.mode = mode; a.err = err;
-  a.ekey = ekey; a.key_r0 = key_r0; a.key_c0 = key_c0;
   if (a.ktiles == 0) return RFM_OK;
   ProfScope ps(PF_OZ_GEMM, st);
   {

@@ -739,7 +739,6 @@ long long rfm_householder_emulated_bytes(long long s, long long n) {
   b += rfm_oz_digit_bytes(n, QB, QDIG, 64);   // W2
   b += 8LL * (2LL * QB * n + nzg * QB * QB + 3LL * QB * QB);
   b += 4LL * (QB + n + s + n) + 4096;
-  b += 4LL * n + 256;  // exponent keys of the next trailing matrix
   return b;
 }
 
@@ -780,8 +779,6 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
   int* e_at = reinterpret_cast<int*>(take(4LL * n));
   int* e_v = reinterpret_cast<int*>(take(4LL * s));
   int* e_w2 = reinterpret_cast<int*>(take(4LL * n));
-  int* keys = reinterpret_cast<int*>(take(4LL * n));  // exponent keys gathered by the previous update
-  bool have_keys = false;
   unsigned int* err = sync + SYNC_ERR;
   RFM_CUDA(cudaMemsetAsync(sync + SYNC_BAR, 0, 2 * sizeof(unsigned int), st));
   const long long cstop = ncols < 0 ? n : std::min<long long>(n, ncols);
@@ -807,11 +804,7 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
     {
       ProfScope ps(PF_QR_VTA, st);
       RFM_TRY(rfm_oz_slice_house_vt(A, lda, J0, nbw, rows, QDIG, e_vt, d_vt, st));
-      if (have_keys)  // the trailing matrix's column exponents came with the last update
-        RFM_TRY(rfm_oz_slice_strided_keys(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, keys, e_at, d_at,
-                                          st));
-      else
-        RFM_TRY(rfm_oz_slice_strided(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, e_at, d_at, st));
+      RFM_TRY(rfm_oz_slice_strided(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, e_at, d_at, st));
       RFM_TRY(rfm_oz_gemm(d_vt, QDIG, e_vt, d_at, QDIG, e_at, nbw, nt, rows, QDIG + 1, Wm, QB, 0, err, st));
       k_block_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(T, Wm, nbw, nt, W2);
       RFM_CHECK_LAUNCH();
@@ -820,13 +813,8 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
       ProfScope ps(PF_QR_UPDATE, st);
       RFM_TRY(rfm_oz_slice_house_v(A, lda, J0, rows, nbw, QDIG, e_v, d_v, st));
       RFM_TRY(rfm_oz_slice_strided(W2, QB, 1, nt, nbw, QDIG, 64, e_w2, d_w2, st));
-      // the next block's trailing matrix (rows from c1, columns from c1 + its
-      // width) is written here; gather its column exponents on the way
-      const long long nbw_next = std::min<long long>(QB, n - c1);
-      have_keys = J0 + QB < cstop && nt > nbw_next;
-      if (have_keys) RFM_CUDA(cudaMemsetAsync(keys, 0, sizeof(int) * (size_t)(nt - nbw_next), st));
       RFM_TRY(rfm_oz_gemm(d_v, QDIG, e_v, d_w2, QDIG, e_w2, rows, nt, nbw, QDIG + 1, A + (size_t)c1 * lda + J0, lda,
-                          1, err, st, have_keys ? keys : nullptr, nbw, nbw_next));
+                          1, err, st));
     }
   }
   return finish_r(A, n, lda, st, q, sync, rank_flag_host);

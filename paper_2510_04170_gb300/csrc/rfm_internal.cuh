@@ -181,13 +181,9 @@ rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* ro
                                int W, int ndig, int* e, uint16_t* out, cudaStream_t st);
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
-                       unsigned* err, cudaStream_t st, int* ekey = nullptr, long long key_r0 = 0,
-                       long long key_c0 = 0);
+                       unsigned* err, cudaStream_t st);
 rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, long long R, long long K, int ndig,
                                 int tile_rows, int* e, uint16_t* out, cudaStream_t st);
-rfm_status rfm_oz_slice_strided_keys(const double* base, long long si, long long sk, long long R, long long K,
-                                     int ndig, int tile_rows, const int* keys, int* e, uint16_t* out,
-                                     cudaStream_t st);
 long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows);
 rfm_status rfm_householder_inplace(double* A, long long s, long long n, long long lda,
                                    cudaStream_t st, double* scratch, long long scratch_len,
