@@ -216,7 +216,7 @@ constexpr int CHAIN_NEAR = 3;          // the chain applies distances 1 .. CHAIN
 constexpr int HMAXT = 4;               // targets per helper CTA
 
 __host__ __device__ constexpr size_t chain_smem_bytes() {
-  return (size_t)(2 * 3 * TTILE + 3 * TB + TB + 8 * TB) * sizeof(double);
+  return (size_t)(2 * 3 * TTILE + 3 * TB + 2 * TB + 2 * TB + 8 * TB) * sizeof(double);
 }
 
 __device__ __forceinline__ void cp_async8(double* dst, const double* src) {
@@ -260,26 +260,6 @@ __device__ __forceinline__ void load_tile(double* T, const double* __restrict__ 
 template <int TRANS>
 __device__ __forceinline__ int chain_block(int t, int nblk) { return TRANS == 0 ? nblk - 1 - t : t; }
 
-// Tiles of step t: the diagonal tile and the coupling tiles to the blocks of
-// order t-1 and t-2 (R(k, j) for R^{-1}: rows of block k, columns of block j;
-// R(j, k) for R^{-T}).  Issued by warps 1-7 only: warp 0 publishes each
-// step's result behind a memory fence, which would otherwise also wait for
-// these copies in flight.
-template <int TRANS>
-__device__ __forceinline__ void chain_tiles(double* stage, const double* __restrict__ R, long long ldr, int n, int nblk,
-                                            int t) {
-  if (threadIdx.x < 32) return;
-  const int first = threadIdx.x - 32, stride = blockDim.x - 32;
-  const int k = chain_block<TRANS>(t, nblk);
-  load_tile(stage, R, ldr, n, k, k, first, stride);
-  for (int d = 1; d < CHAIN_NEAR; ++d) {
-    if (t - d < 0) break;
-    const int j = chain_block<TRANS>(t - d, nblk);
-    if (TRANS == 0) load_tile(stage + d * TTILE, R, ldr, n, k, j, first, stride);
-    else load_tile(stage + d * TTILE, R, ldr, n, j, k, first, stride);
-  }
-}
-
 struct ChainArgs {
   const double* R;
   long long ldr;
@@ -303,34 +283,90 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
   const int nblk = a.nblk, n = a.n;
   if (blockIdx.x == 0) {
     // ------------------------------------------------------------ chain
-    double* stages = csm;                  // 2 stages x 3 tiles
-    double* xh = csm + 2 * 3 * TTILE;      // x of the last three steps [3][64]
-    double* srec = xh + 3 * TB;            // reciprocals of the diagonal [64]
-    double* sred = srec + TB;              // [8][64] partial sums
-    chain_tiles<TRANS>(stages, a.R, a.ldr, n, nblk, 0);
-    cp_async_commit();
-    for (int t = 0; t < nblk; ++t) {
-      double* st = stages + (t & 1) * 3 * TTILE;
-      if (t + 1 < nblk) chain_tiles<TRANS>(stages + ((t + 1) & 1) * 3 * TTILE, a.R, a.ldr, n, nblk, t + 1);
+    // Step t solves block k_t.  On its critical path: the coupling to the
+    // block solved just before (tile C1_t times x_{t-1}, all warps), then
+    // warp 0's substitution with the diagonal tile prescaled by the pivot
+    // reciprocals (one dependent FMA per row).  Everything else for step
+    // t + 1 is prepared by warps 1-7 while warp 0 substitutes: the copies of
+    // D_{t+1}, C1_{t+1} and C2_{t+2} (two commit groups), the reciprocals and
+    // prescaling of D_{t+1}, and the distance-2 contribution C2_{t+1} x_{t-1}.
+    double* Dbuf = csm;                        // [2] diagonal tiles, prescaled
+    double* C1buf = Dbuf + 2 * TTILE;          // [2] coupling to the previous block
+    double* C2buf = C1buf + 2 * TTILE;         // [2] coupling to the block before that
+    double* xh = C2buf + 2 * TTILE;            // x of the last three steps [3][64]
+    double* srec = xh + 3 * TB;                // [2][64] pivot reciprocals
+    double* dist2 = srec + 2 * TB;             // [2][64] distance-2 contributions
+    double* sred = dist2 + 2 * TB;             // [8][64] partial sums
+    auto issue_dc1 = [&](int tt) {             // D_tt and C1_tt
+      const int k = chain_block<TRANS>(tt, nblk);
+      load_tile(Dbuf + (tt & 1) * TTILE, a.R, a.ldr, n, k, k, tid - 32, 224);
+      if (tt >= 1) {
+        const int j = chain_block<TRANS>(tt - 1, nblk);
+        if (TRANS == 0) load_tile(C1buf + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, tid - 32, 224);
+        else load_tile(C1buf + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, tid - 32, 224);
+      }
+    };
+    auto issue_c2 = [&](int tt) {              // C2_tt
+      if (tt >= 2 && tt < nblk) {
+        const int k = chain_block<TRANS>(tt, nblk), j = chain_block<TRANS>(tt - 2, nblk);
+        if (TRANS == 0) load_tile(C2buf + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, tid - 32, 224);
+        else load_tile(C2buf + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, tid - 32, 224);
+      }
+    };
+    // prepare step tt (warps 1-7): reciprocals, prescaling, distance-2 part
+    auto prepare = [&](int tt) {
+      const int k = chain_block<TRANS>(tt, nblk);
+      const int rows = min(TB, n - k * TB);
+      double* D = Dbuf + (tt & 1) * TTILE;
+      double* rc = srec + (tt & 1) * TB;
+      if (tid - 32 < TB) rc[tid - 32] = (tid - 32) < rows ? 1.0 / D[(tid - 32) * TLD + (tid - 32)] : 0.0;
+      asm volatile("bar.sync 1, 224;" ::: "memory");
+      // TRANS 0 scales column i of D by rec_i, TRANS 1 row i (off-diagonal entries)
+      for (int idx = tid - 32; idx < TB * TB; idx += 224) {
+        const int r = idx & (TB - 1), c = idx >> 6;
+        if (r < c) D[c * TLD + r] *= (TRANS == 0 ? rc[c] : rc[r]);
+      }
+      double* d2 = dist2 + (tt & 1) * TB;
+      if (tt >= 2) {
+        const double* T = C2buf + (tt & 1) * TTILE;
+        const double* xv = xh + ((tt - 2) % 3) * TB;
+        for (int x = tid - 32; x < TB; x += 224) {
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};  // four independent sums
+#pragma unroll 4
+          for (int y = 0; y < TB; ++y)
+            acc[y & 3] += (TRANS == 0 ? T[y * TLD + x] : T[x * TLD + y]) * xv[y];
+          d2[x] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        }
+      } else if (tid - 32 < TB) {
+        d2[tid - 32] = 0.0;
+      }
+    };
+    if (w >= 1) {
+      issue_dc1(0);
       cp_async_commit();
-      cp_async_wait1();
-      __syncthreads();
+      issue_c2(1);  // none
+      cp_async_commit();
+      cp_async_wait0();
+      asm volatile("bar.sync 1, 224;" ::: "memory");
+      prepare(0);
+    }
+    __syncthreads();
+    for (int t = 0; t < nblk; ++t) {
       const int k = chain_block<TRANS>(t, nblk);
       const int r0 = k * TB, rows = min(TB, n - r0);
-      if (tid < TB) srec[tid] = tid < rows ? 1.0 / st[tid * TLD + tid] : 0.0;
-      // contributions of the blocks at distance 1 and 2 (tiles in shared memory)
+      // critical: coupling to the block solved just before
       double p0 = 0.0, p1 = 0.0;
-      for (int d = 1; d < CHAIN_NEAR && t - d >= 0; ++d) {
-        const double* T = st + d * TTILE;
-        const double* xv = xh + ((t - d) % 3) * TB;
+      if (t >= 1) {
+        const double* T = C1buf + (t & 1) * TTILE;
+        const double* xv = xh + ((t - 1) % 3) * TB;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int y = w + 8 * q;
           const double v = xv[y];
-          if (TRANS == 0) {  // target row lane / lane+32, source column y
+          if (TRANS == 0) {
             p0 += T[y * TLD + lane] * v;
             p1 += T[y * TLD + lane + 32] * v;
-          } else {           // target column lane / lane+32, source row y
+          } else {
             p0 += T[lane * TLD + y] * v;
             p1 += T[(lane + 32) * TLD + y] * v;
           }
@@ -338,52 +374,58 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
       }
       sred[w * TB + lane] = p0;
       sred[w * TB + lane + 32] = p1;
-      // helper partial sums of the distances >= 3
       if (t >= CHAIN_NEAR && tid == 0) wait_flag(a.accflag + k, epoch, a.err);
       __syncthreads();
       if (w == 0) {
+        const double* rc = srec + (t & 1) * TB;
+        const double* d2 = dist2 + (t & 1) * TB;
         double acc[2];
+#pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int rr = lane + 32 * h;
-          double sm = 0.0;
+          double sm = d2[rr];
 #pragma unroll
           for (int q = 0; q < 8; ++q) sm += sred[q * TB + rr];
           if (t >= CHAIN_NEAR) sm += __ldcg(a.accbuf + (size_t)k * TB + rr);
           acc[h] = rr < rows ? a.rhs[r0 + rr] - sm : 0.0;
         }
-        const double* D = st;  // D(r, c) = D[c * TLD + r]
-        double xv[2] = {0.0, 0.0};
-        // fully unrolled so that acc[] and xv[] stay in registers (the pivot
-        // index is a compile-time constant in every step)
+        const double* D = Dbuf + (t & 1) * TTILE;  // prescaled: D'(r, c) = D[c * TLD + r]
+        // one dependent FMA per row: acc_r -= D'(r, i) acc_i, and x_r = acc_r rec_r
         if (TRANS == 0) {
 #pragma unroll
           for (int i = TB - 1; i >= 0; --i) {
             if (i >= rows) continue;
-            const int hh = i >> 5, ln = i & 31;
-            const double xi = __shfl_sync(0xffffffffu, acc[hh], ln) * srec[i];
-            if (lane == ln) xv[hh] = xi;
-            if (lane < i) acc[0] -= D[i * TLD + lane] * xi;
-            if (lane + 32 < i) acc[1] -= D[i * TLD + lane + 32] * xi;
+            const double ai = __shfl_sync(0xffffffffu, acc[i >> 5], i & 31);
+            if (lane < i) acc[0] -= D[i * TLD + lane] * ai;
+            if (lane + 32 < i) acc[1] -= D[i * TLD + lane + 32] * ai;
           }
         } else {
 #pragma unroll
           for (int i = 0; i < TB; ++i) {
             if (i >= rows) continue;
-            const int hh = i >> 5, ln = i & 31;
-            const double xi = __shfl_sync(0xffffffffu, acc[hh], ln) * srec[i];
-            if (lane == ln) xv[hh] = xi;
-            if (lane > i) acc[0] -= D[lane * TLD + i] * xi;
-            if (lane + 32 > i) acc[1] -= D[(lane + 32) * TLD + i] * xi;
+            const double ai = __shfl_sync(0xffffffffu, acc[i >> 5], i & 31);
+            if (lane > i) acc[0] -= D[lane * TLD + i] * ai;
+            if (lane + 32 > i) acc[1] -= D[(lane + 32) * TLD + i] * ai;
           }
         }
+        const double xv0 = acc[0] * rc[lane], xv1 = acc[1] * rc[lane + 32];
         double* xs = xh + (t % 3) * TB;
-        xs[lane] = xv[0];
-        xs[lane + 32] = xv[1];
-        if (lane < rows) a.x[r0 + lane] = xv[0];
-        if (lane + 32 < rows) a.x[r0 + lane + 32] = xv[1];
+        xs[lane] = xv0;
+        xs[lane + 32] = xv1;
+        if (lane < rows) a.x[r0 + lane] = xv0;
+        if (lane + 32 < rows) a.x[r0 + lane + 32] = xv1;
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(a.prog, (unsigned int)(t + 1));
+      } else if (t + 1 < nblk) {
+        // warps 1-7: tiles for the next steps, then prepare step t + 1
+        issue_dc1(t + 1);
+        cp_async_commit();
+        issue_c2(t + 2);
+        cp_async_commit();
+        cp_async_wait1();  // all but the C2_{t+2} group
+        asm volatile("bar.sync 1, 224;" ::: "memory");
+        prepare(t + 1);
       }
       __syncthreads();
     }
