@@ -529,7 +529,7 @@ rfm_status do_qr(rfm_problem* p) {
   p->ldr = p->s;
   p->have_r = true;
   p->rank_flag = flag;
-  return RFM_OK;
+  return rfm_trsv_prepare(p);
 }
 
 // ---------------------------------------------------------------- LSQR
@@ -953,6 +953,7 @@ rfm_status rfm_problem_create(const rfm_problem_desc* desc, void* cuda_stream, r
     TRYA(dalloc(&p->hsign, p->m));
     TRYA(dalloc(&p->red, 4096));
     TRYA(dalloc(&p->trsv_acc, (size_t)((p->n + 63) / 64) * 64));
+    TRYA(dalloc(&p->dinv, (size_t)((p->n + 63) / 64) * 64 * 64));
     TRYA(dalloc(&p->sync, RFM_SYNC_WORDS));
     p->work_cap = vec_stride(p) * WV_COUNT;
     TRYA(dalloc(&p->work, p->work_cap));
@@ -1005,7 +1006,7 @@ rfm_status rfm_problem_destroy(rfm_problem* p) {
   void* bufs[] = {p->X, p->mu, p->sig, p->feat, p->segs, p->pts, p->rmeta, p->rhs, p->Jp, p->Js, p->lam, p->F,
                   p->colptr, p->colrows, p->B, p->Sg, p->hbuck, p->hsign, p->bptr, p->brows, p->Rown, p->work,
                   p->red, p->sync, p->sdig, p->jdig, p->oz_e, p->oz_toff, p->qr_emu, p->qr_scratch,
-                  p->trsv_acc};
+                  p->trsv_acc, p->dinv};
   drop_lsqr_graph(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void* b : bufs) dfree(b);
@@ -1050,6 +1051,7 @@ rfm_status rfm_assemble(rfm_problem* p, const double* c_dev, double c_scale, dou
   RFM_TRY(rfm_launch_assemble(p, c_dev, c_scale, true, nullptr, p->F));
   p->have_j = true;
   p->have_r = false;
+  p->dinv_of = nullptr;
   if (F_dev) RFM_CUDA(cudaMemcpyAsync(F_dev, p->F, p->m * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   if (lam_dev) RFM_CUDA(cudaMemcpyAsync(lam_dev, p->lam, p->m * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   RFM_CUDA(cudaStreamSynchronize(p->stream));
@@ -1124,6 +1126,7 @@ rfm_status rfm_sketch(rfm_problem* p, int kind, int64_t s, int kJ, double* B_dev
   RFM_TRY(clear_err(p));
   RFM_TRY(do_sketch(p, kind, s, kJ));
   p->have_r = false;
+  p->dinv_of = nullptr;
   if (B_dev) RFM_CUDA(cudaMemcpyAsync(B_dev, p->B, (size_t)s * p->n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   RFM_CUDA(cudaStreamSynchronize(p->stream));
   return RFM_OK;
@@ -1152,6 +1155,7 @@ rfm_status rfm_set_r(rfm_problem* p, const double* R_dev) {
   p->R = p->Rown;
   p->ldr = p->n;
   p->have_r = true;
+  RFM_TRY(rfm_trsv_prepare(p));
   RFM_CUDA(cudaStreamSynchronize(p->stream));
   return RFM_OK;
 }

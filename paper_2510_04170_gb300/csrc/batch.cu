@@ -155,6 +155,7 @@ void release_workspace(rfm_problem* p) {
   p->qr_emu_bytes = p->qr_scratch_len = p->sdig_bytes = p->jdig_bytes = 0;
   p->R = nullptr;
   p->have_r = false;
+  p->dinv_of = nullptr;
   if (p->lsqr_graph) cudaGraphExecDestroy((cudaGraphExec_t)p->lsqr_graph);
   p->lsqr_graph = nullptr;
   p->lsqr_graph_key = 0;

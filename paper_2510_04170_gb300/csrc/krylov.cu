@@ -200,23 +200,25 @@ __global__ void __launch_bounds__(256) k_trsv(const double* __restrict__ R, long
 // Triangular solve as one chain CTA plus helper CTAs (cooperative launch, all
 // CTAs co-resident).  The 64-row blocks are solved in dependency order
 // t = 0, 1, ... (block nblk-1-t for R^{-1}, block t for R^{-T}).  The chain
-// CTA solves the diagonal blocks one after another; before step t it has the
-// diagonal tile and the tiles coupling block t to the two blocks solved just
-// before (order distance 1 and 2) in shared memory (cp.async, issued one step
-// ahead), so its step reads no global memory except the right-hand side and
-// one partial sum.  The helper CTAs add the contributions of all earlier
-// blocks (distance >= 3) as soon as each block is published: helper h owns
-// the targets t = 3 + (h - 1) + H m, streams their tiles of R (each read
-// once), and publishes each target's partial sum three steps before the
-// chain needs it.  All sums are in a fixed order, so results are
-// deterministic.  Waits are bounded (wait_flag).
+// CTA solves the diagonal blocks one after another, with the inverse Z_k of
+// each 64 x 64 diagonal block, computed once per factorisation
+// (k_trsv_dinv): x_k = Z_k (b_k - sum_j R_kj x_j), two dense products and no
+// dependent substitution.  It holds Z_k and the tiles coupling block k to the
+// two blocks solved just before (order distance 1 and 2) in shared memory
+// (cp.async, issued ahead), so its step reads no global memory except the
+// right-hand side and one partial sum.  The helper CTAs add the
+// contributions of all earlier blocks (distance >= 3) as soon as each block
+// is published: helper h owns the targets t = 3 + (h - 1) + H m, streams
+// their tiles of R (each read once), and publishes each target's partial sum
+// three steps before the chain needs it.  All sums are in a fixed order, so
+// results are deterministic.  Waits are bounded (wait_flag).
 constexpr int TLD = TB + 2;            // leading dimension of a shared-memory tile (doubles; 16-byte rows)
 constexpr int TTILE = TB * TLD;        // doubles per shared-memory tile
 constexpr int CHAIN_NEAR = 3;          // the chain applies distances 1 .. CHAIN_NEAR-1 itself
 constexpr int HMAXT = 4;               // targets per helper CTA
 
 __host__ __device__ constexpr size_t chain_smem_bytes() {
-  return (size_t)(2 * 3 * TTILE + 3 * TB + 2 * TB + 2 * TB + 8 * TB) * sizeof(double);
+  return (size_t)(2 * 3 * TTILE + 3 * TB + TB + 2 * TB) * sizeof(double);
 }
 
 __device__ __forceinline__ void cp_async8(double* dst, const double* src) {
@@ -231,6 +233,7 @@ __device__ __forceinline__ void cp_async16(double* dst, const double* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Tile of R with row block a and column block b into shared memory,
@@ -260,8 +263,42 @@ __device__ __forceinline__ void load_tile(double* T, const double* __restrict__ 
 template <int TRANS>
 __device__ __forceinline__ int chain_block(int t, int nblk) { return TRANS == 0 ? nblk - 1 - t : t; }
 
+// Inverse of each 64 x 64 diagonal block of R, block k stored column-major at
+// Z + k * 4096: Z[k][c * 64 + r] = (R_kk^{-1})(r, c).  Entries below the
+// diagonal and, in a ragged last block, rows and columns past n are zero.
+// Column c solves R_kk z = e_c by back substitution (one warp per column,
+// rows on the lanes, IEEE division by each pivot).
+__global__ void __launch_bounds__(256) k_trsv_dinv(const double* __restrict__ R, long long ldr, int n,
+                                                   double* __restrict__ Z) {
+  __shared__ double D[TB * TLD];
+  const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int r0 = k * TB, rows = min(TB, n - r0);
+  for (int idx = tid; idx < TB * TB; idx += blockDim.x) {
+    const int r = idx & (TB - 1), c = idx >> 6;
+    D[c * TLD + r] = (r <= c && c < rows) ? R[(size_t)(r0 + c) * ldr + r0 + r] : 0.0;
+  }
+  __syncthreads();
+  double* out = Z + (size_t)k * TB * TB;
+  for (int j = w; j < TB; j += 8) {
+    double acc0 = lane == j ? 1.0 : 0.0, acc1 = lane + 32 == j ? 1.0 : 0.0;
+    double z0 = 0.0, z1 = 0.0;
+    if (j < rows) {
+      for (int i = j; i >= 0; --i) {
+        const double zi = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31) / D[i * TLD + i];
+        if (i < 32 && lane == i) z0 = zi;
+        if (i >= 32 && lane == i - 32) z1 = zi;
+        if (lane < i) acc0 -= D[i * TLD + lane] * zi;
+        if (lane + 32 < i) acc1 -= D[i * TLD + lane + 32] * zi;
+      }
+    }
+    out[j * TB + lane] = z0;
+    out[j * TB + lane + 32] = z1;
+  }
+}
+
 struct ChainArgs {
   const double* R;
+  const double* Z;            // inverses of the diagonal blocks (k_trsv_dinv)
   long long ldr;
   int n, nblk, H;
   const double* rhs;
@@ -283,151 +320,114 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
   const int nblk = a.nblk, n = a.n;
   if (blockIdx.x == 0) {
     // ------------------------------------------------------------ chain
-    // Step t solves block k_t.  On its critical path: the coupling to the
-    // block solved just before (tile C1_t times x_{t-1}, all warps), then
-    // warp 0's substitution with the diagonal tile prescaled by the pivot
-    // reciprocals (one dependent FMA per row).  Everything else for step
-    // t + 1 is prepared by warps 1-7 while warp 0 substitutes: the copies of
-    // D_{t+1}, C1_{t+1} and C2_{t+2} (two commit groups), the reciprocals and
-    // prescaling of D_{t+1}, and the distance-2 contribution C2_{t+1} x_{t-1}.
-    double* Dbuf = csm;                        // [2] diagonal tiles, prescaled
-    double* C1buf = Dbuf + 2 * TTILE;          // [2] coupling to the previous block
-    double* C2buf = C1buf + 2 * TTILE;         // [2] coupling to the block before that
-    double* xh = C2buf + 2 * TTILE;            // x of the last three steps [3][64]
-    double* srec = xh + 3 * TB;                // [2][64] pivot reciprocals
-    double* dist2 = srec + 2 * TB;             // [2][64] distance-2 contributions
-    double* sred = dist2 + 2 * TB;             // [8][64] partial sums
-    auto issue_dc1 = [&](int tt) {             // D_tt and C1_tt
+    // Warps 0-3 take step t's critical path: y = b_k - (helper sum) -
+    // (distance-2 sum) - C1_t x_{t-1}, then x_t = Z_k y, two threads per row
+    // (each a fixed half of the terms).  Warps 4-7 meanwhile publish x_{t-1},
+    // issue the copies of Z and C1 for step t + 1 and of C2 for step t + 2,
+    // form the distance-2 sum of step t + 1 (C2_{t+1} x_{t-1}) and acquire
+    // the helpers' sum for step t + 1.
+    double* Zb = csm;                          // [2] inverse diagonal tiles
+    double* C1b = Zb + 2 * TTILE;              // [2] coupling to the previous block
+    double* C2b = C1b + 2 * TTILE;             // [2] coupling to the block before that
+    double* xh = C2b + 2 * TTILE;              // x of the last three steps [3][64]
+    double* ys = xh + 3 * TB;                  // [64] right-hand side of the diagonal block
+    double* d2s = ys + TB;                     // [2][64] distance-2 sums
+    const bool crit = w < 4;
+    const int ct = crit ? tid : tid - 128;     // thread index within its group of 128
+    const int r = ct >> 1, hh = ct & 1;        // row and half
+    // Term i (0..31) of half hh: the column index of a tile row.  The order
+    // keeps a warp's shared-memory reads on distinct banks: T[term * TLD + r]
+    // for TRANS 0, T[r * TLD + term] for TRANS 1.
+    auto term = [&](int i) { return TRANS == 0 ? (i & 3) + 8 * (i >> 2) + 4 * hh : 2 * i + hh; };
+    auto tile_dot = [&](const double* T, const double* v, int i0, int i1) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int i = i0; i < i1; i += 4) {
+        const int y0 = term(i), y1 = term(i + 1), y2 = term(i + 2), y3 = term(i + 3);
+        if (TRANS == 0) {
+          s0 += T[y0 * TLD + r] * v[y0];
+          s1 += T[y1 * TLD + r] * v[y1];
+          s2 += T[y2 * TLD + r] * v[y2];
+          s3 += T[y3 * TLD + r] * v[y3];
+        } else {
+          s0 += T[r * TLD + y0] * v[y0];
+          s1 += T[r * TLD + y1] * v[y1];
+          s2 += T[r * TLD + y2] * v[y2];
+          s3 += T[r * TLD + y3] * v[y3];
+        }
+      }
+      const double s = (s0 + s1) + (s2 + s3);
+      return s + __shfl_xor_sync(0xffffffffu, s, 1);
+    };
+    auto issue_zc1 = [&](int tt) {             // Z_tt and C1_tt
       const int k = chain_block<TRANS>(tt, nblk);
-      load_tile(Dbuf + (tt & 1) * TTILE, a.R, a.ldr, n, k, k, tid - 32, 224);
+      const double* src = a.Z + (size_t)k * TB * TB;
+      double* dst = Zb + (tt & 1) * TTILE;
+      for (int idx = ct; idx < TB * TB / 2; idx += 128) {
+        const int rr = (idx & (TB / 2 - 1)) * 2, cc = idx >> 5;
+        cp_async16(dst + cc * TLD + rr, src + cc * TB + rr);
+      }
       if (tt >= 1) {
         const int j = chain_block<TRANS>(tt - 1, nblk);
-        if (TRANS == 0) load_tile(C1buf + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, tid - 32, 224);
-        else load_tile(C1buf + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, tid - 32, 224);
+        if (TRANS == 0) load_tile(C1b + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, ct, 128);
+        else load_tile(C1b + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, ct, 128);
       }
     };
     auto issue_c2 = [&](int tt) {              // C2_tt
       if (tt >= 2 && tt < nblk) {
         const int k = chain_block<TRANS>(tt, nblk), j = chain_block<TRANS>(tt - 2, nblk);
-        if (TRANS == 0) load_tile(C2buf + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, tid - 32, 224);
-        else load_tile(C2buf + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, tid - 32, 224);
+        if (TRANS == 0) load_tile(C2b + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, ct, 128);
+        else load_tile(C2b + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, ct, 128);
       }
     };
-    // prepare step tt (warps 1-7): reciprocals, prescaling, distance-2 part
-    auto prepare = [&](int tt) {
-      const int k = chain_block<TRANS>(tt, nblk);
-      const int rows = min(TB, n - k * TB);
-      double* D = Dbuf + (tt & 1) * TTILE;
-      double* rc = srec + (tt & 1) * TB;
-      if (tid - 32 < TB) rc[tid - 32] = (tid - 32) < rows ? 1.0 / D[(tid - 32) * TLD + (tid - 32)] : 0.0;
-      asm volatile("bar.sync 1, 224;" ::: "memory");
-      // TRANS 0 scales column i of D by rec_i, TRANS 1 row i (off-diagonal entries)
-      for (int idx = tid - 32; idx < TB * TB; idx += 224) {
-        const int r = idx & (TB - 1), c = idx >> 6;
-        if (r < c) D[c * TLD + r] *= (TRANS == 0 ? rc[c] : rc[r]);
-      }
-      double* d2 = dist2 + (tt & 1) * TB;
-      if (tt >= 2) {
-        const double* T = C2buf + (tt & 1) * TTILE;
-        const double* xv = xh + ((tt - 2) % 3) * TB;
-        for (int x = tid - 32; x < TB; x += 224) {
-          double acc[4] = {0.0, 0.0, 0.0, 0.0};  // four independent sums
-#pragma unroll 4
-          for (int y = 0; y < TB; ++y)
-            acc[y & 3] += (TRANS == 0 ? T[y * TLD + x] : T[x * TLD + y]) * xv[y];
-          d2[x] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-        }
-      } else if (tid - 32 < TB) {
-        d2[tid - 32] = 0.0;
-      }
-    };
-    if (w >= 1) {
-      issue_dc1(0);
-      cp_async_commit();
-      issue_c2(1);  // none
+    // the terms of Z's row r that can be nonzero, at warp granularity:
+    // TRANS 0 (upper) columns >= 16 w, TRANS 1 (lower) columns < 16 (w + 1)
+    const int zi0 = TRANS == 0 ? 8 * w : 0, zi1 = TRANS == 0 ? 32 : 8 * (w + 1);
+    if (!crit) {
+      issue_zc1(0);
       cp_async_commit();
       cp_async_wait0();
-      asm volatile("bar.sync 1, 224;" ::: "memory");
-      prepare(0);
+      if (ct < TB) d2s[ct] = 0.0;
     }
     __syncthreads();
     for (int t = 0; t < nblk; ++t) {
-      const int k = chain_block<TRANS>(t, nblk);
-      const int r0 = k * TB, rows = min(TB, n - r0);
-      // critical: coupling to the block solved just before
-      double p0 = 0.0, p1 = 0.0;
-      if (t >= 1) {
-        const double* T = C1buf + (t & 1) * TTILE;
-        const double* xv = xh + ((t - 1) % 3) * TB;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int y = w + 8 * q;
-          const double v = xv[y];
-          if (TRANS == 0) {
-            p0 += T[y * TLD + lane] * v;
-            p1 += T[y * TLD + lane + 32] * v;
-          } else {
-            p0 += T[lane * TLD + y] * v;
-            p1 += T[(lane + 32) * TLD + y] * v;
-          }
+      if (crit) {
+        const int k = chain_block<TRANS>(t, nblk);
+        const int r0 = k * TB, rows = min(TB, n - r0);
+        double base = r < rows ? a.rhs[r0 + r] : 0.0;
+        if (t >= CHAIN_NEAR) base -= __ldcg(a.accbuf + (size_t)k * TB + r);
+        base -= d2s[(t & 1) * TB + r];
+        const double p = t >= 1 ? tile_dot(C1b + (t & 1) * TTILE, xh + ((t + 2) % 3) * TB, 0, 32) : 0.0;
+        if (hh == 0) ys[r] = base - p;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const double xr = tile_dot(Zb + (t & 1) * TTILE, ys, zi0, zi1);
+        if (hh == 0) {
+          xh[(t % 3) * TB + r] = xr;
+          if (r < rows) a.x[r0 + r] = xr;
         }
-      }
-      sred[w * TB + lane] = p0;
-      sred[w * TB + lane + 32] = p1;
-      if (t >= CHAIN_NEAR && tid == 0) wait_flag(a.accflag + k, epoch, a.err);
-      __syncthreads();
-      if (w == 0) {
-        const double* rc = srec + (t & 1) * TB;
-        const double* d2 = dist2 + (t & 1) * TB;
-        double acc[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int rr = lane + 32 * h;
-          double sm = d2[rr];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) sm += sred[q * TB + rr];
-          if (t >= CHAIN_NEAR) sm += __ldcg(a.accbuf + (size_t)k * TB + rr);
-          acc[h] = rr < rows ? a.rhs[r0 + rr] - sm : 0.0;
+      } else {
+        if (ct == 0 && t >= 1) {  // blocks 0 .. t-1 are in a.x (barrier at the end of step t-1)
+          __threadfence();
+          st_release(a.prog, (unsigned int)t);
         }
-        const double* D = Dbuf + (t & 1) * TTILE;  // prescaled: D'(r, c) = D[c * TLD + r]
-        // one dependent FMA per row: acc_r -= D'(r, i) acc_i, and x_r = acc_r rec_r
-        if (TRANS == 0) {
-#pragma unroll
-          for (int i = TB - 1; i >= 0; --i) {
-            if (i >= rows) continue;
-            const double ai = __shfl_sync(0xffffffffu, acc[i >> 5], i & 31);
-            if (lane < i) acc[0] -= D[i * TLD + lane] * ai;
-            if (lane + 32 < i) acc[1] -= D[i * TLD + lane + 32] * ai;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < TB; ++i) {
-            if (i >= rows) continue;
-            const double ai = __shfl_sync(0xffffffffu, acc[i >> 5], i & 31);
-            if (lane > i) acc[0] -= D[lane * TLD + i] * ai;
-            if (lane + 32 > i) acc[1] -= D[(lane + 32) * TLD + i] * ai;
-          }
-        }
-        const double xv0 = acc[0] * rc[lane], xv1 = acc[1] * rc[lane + 32];
-        double* xs = xh + (t % 3) * TB;
-        xs[lane] = xv0;
-        xs[lane + 32] = xv1;
-        if (lane < rows) a.x[r0 + lane] = xv0;
-        if (lane + 32 < rows) a.x[r0 + lane + 32] = xv1;
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release(a.prog, (unsigned int)(t + 1));
-      } else if (t + 1 < nblk) {
-        // warps 1-7: tiles for the next steps, then prepare step t + 1
-        issue_dc1(t + 1);
+        if (t + 1 < nblk) issue_zc1(t + 1);
         cp_async_commit();
         issue_c2(t + 2);
         cp_async_commit();
-        cp_async_wait1();  // all but the C2_{t+2} group
-        asm volatile("bar.sync 1, 224;" ::: "memory");
-        prepare(t + 1);
+        cp_async_wait2();  // C2_{t+1}, issued one step earlier
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (t + 1 < nblk) {
+          const double p = t + 1 >= 2 ? tile_dot(C2b + ((t + 1) & 1) * TTILE, xh + ((t + 2) % 3) * TB, 0, 32) : 0.0;
+          if (hh == 0) d2s[((t + 1) & 1) * TB + r] = p;
+          if (ct == 0 && t + 1 >= CHAIN_NEAR)
+            wait_flag(a.accflag + chain_block<TRANS>(t + 1, nblk), epoch, a.err);
+        }
+        cp_async_wait1();  // Z_{t+1} and C1_{t+1}
       }
       __syncthreads();
+    }
+    if (!crit && ct == 0) {
+      __threadfence();
+      st_release(a.prog, (unsigned int)nblk);
     }
     cp_async_wait0();
     return;
@@ -640,6 +640,15 @@ rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y) {
   return RFM_OK;
 }
 
+rfm_status rfm_trsv_prepare(rfm_problem* p) {
+  if (!p->dinv || !p->R) return RFM_OK;
+  const int n = (int)p->n;
+  k_trsv_dinv<<<(n + TB - 1) / TB, 256, 0, p->stream>>>(p->R, p->ldr, n, p->dinv);
+  RFM_CHECK_LAUNCH();
+  p->dinv_of = p->R;
+  return RFM_OK;
+}
+
 rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x) {
   const int n = (int)p->n;
   const int nblk = (n + TB - 1) / TB;
@@ -647,6 +656,7 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
     rfm_set_error("trsv: too many blocks");
     return RFM_EINVAL;
   }
+  if (p->dinv && p->dinv_of != p->R) RFM_TRY(rfm_trsv_prepare(p));
   k_trsv_prep<<<1, 1, 0, p->stream>>>(p->sync + SYNC_EPOCH, p->sync + SYNC_TICKET);
   RFM_CHECK_LAUNCH();
   ProfScope ps(PF_TRSV, p->stream);
@@ -654,9 +664,9 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
   // chain + helpers when every target past distance 2 has a helper slot
   const int nsm = rfm_num_sms();
   const int H = nblk > CHAIN_NEAR ? std::min(nsm - 1, nblk - CHAIN_NEAR) : 0;
-  if (p->trsv_acc && nsm > 1 && nblk - CHAIN_NEAR <= HMAXT * H) {
+  if (p->trsv_acc && p->dinv && nsm > 1 && nblk - CHAIN_NEAR <= HMAXT * H) {
     ChainArgs a;
-    a.R = p->R; a.ldr = p->ldr; a.n = n; a.nblk = nblk; a.H = H; a.rhs = b; a.x = x;
+    a.R = p->R; a.Z = p->dinv; a.ldr = p->ldr; a.n = n; a.nblk = nblk; a.H = H; a.rhs = b; a.x = x;
     a.accbuf = p->trsv_acc; a.accflag = p->sync + SYNC_FLAGS; a.prog = p->sync + SYNC_TICKET;
     a.epoch_dev = p->sync + SYNC_EPOCH; a.err = p->sync + SYNC_ERR; a.skip = p->skip;
     const void* fn = trans == 0 ? (const void*)k_trsv_chain<0> : (const void*)k_trsv_chain<1>;

@@ -98,6 +98,8 @@ struct rfm_problem {
   bool lsqr_eager = false;        // graph capture failed once: replay the chunk's kernels eagerly
   int qr_panel_cap = 0;           // most CTAs per panel factorisation (0: one per SM)
   double* trsv_acc = nullptr;     // [ceil(n/64)][64] partial sums of the triangular solve's helpers
+  double* dinv = nullptr;         // [ceil(n/64)][64 x 64] inverses of R's diagonal blocks (column-major)
+  const double* dinv_of = nullptr;  // the R that dinv was computed from (nullptr: stale)
   // per-problem QR scratch (FP64 panel buffers)
   double* qr_scratch = nullptr;
   long long qr_scratch_len = 0;
@@ -169,6 +171,7 @@ rfm_status rfm_launch_phi_values(const rfm_problem* p, const double* pts, long l
 rfm_status rfm_launch_jmv(rfm_problem* p, const double* x, double* y);
 rfm_status rfm_launch_jtmv(rfm_problem* p, const double* x, double* y);
 rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x);
+rfm_status rfm_trsv_prepare(rfm_problem* p);  // inverts R's diagonal blocks (after every change of R)
 rfm_status rfm_launch_count_sketch(rfm_problem* p, long long s, int kJ);
 rfm_status rfm_launch_gauss_sketch(rfm_problem* p, long long s, int kJ);
 rfm_status rfm_launch_gauss_sketch_tc(rfm_problem* p, long long s, int kJ);
