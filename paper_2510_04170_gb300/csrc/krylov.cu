@@ -218,7 +218,7 @@ constexpr int CHAIN_NEAR = 3;          // the chain applies distances 1 .. CHAIN
 constexpr int HMAXT = 4;               // targets per helper CTA
 
 __host__ __device__ constexpr size_t chain_smem_bytes() {
-  return (size_t)(2 * 3 * TTILE + 3 * TB + TB + 2 * TB) * sizeof(double);
+  return (size_t)(2 * 3 * TTILE + 3 * TB + TB + 2 * TB + 2 * TB) * sizeof(double);
 }
 
 __device__ __forceinline__ void cp_async8(double* dst, const double* src) {
@@ -320,21 +320,23 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
   const int nblk = a.nblk, n = a.n;
   if (blockIdx.x == 0) {
     // ------------------------------------------------------------ chain
-    // Warps 0-3 take step t's critical path: y = b_k - (helper sum) -
-    // (distance-2 sum) - C1_t x_{t-1}, then x_t = Z_k y, two threads per row
-    // (each a fixed half of the terms).  Warps 4-7 meanwhile publish x_{t-1},
-    // issue the copies of Z and C1 for step t + 1 and of C2 for step t + 2,
-    // form the distance-2 sum of step t + 1 (C2_{t+1} x_{t-1}) and acquire
-    // the helpers' sum for step t + 1.
-    double* Zb = csm;                          // [2] inverse diagonal tiles
-    double* C1b = Zb + 2 * TTILE;              // [2] coupling to the previous block
-    double* C2b = C1b + 2 * TTILE;             // [2] coupling to the block before that
-    double* xh = C2b + 2 * TTILE;              // x of the last three steps [3][64]
+    // Warps 0-3 take step t's critical path: y = base_t - C1_t x_{t-1}, then
+    // x_t = Z_k y, two threads per row (each a fixed half of the terms), with
+    // base_t = b_k - (helper sum) - (distance-2 sum) prepared one step ahead.
+    // Warps 4-7 meanwhile publish x_{t-1}, issue the copies of Z and C1 for
+    // step t + 2, form the distance-2 sum of step t + 1 (C2_{t+1} x_{t-1},
+    // with C2_{t+1} fetched into registers one step earlier), fetch C2_{t+2},
+    // acquire the helpers' sum of step t + 1 and form base_{t+1}.
+    double* Zb = csm;                          // [3] inverse diagonal tiles
+    double* C1b = Zb + 3 * TTILE;              // [3] coupling to the previous block
+    double* xh = C1b + 3 * TTILE;              // x of the last three steps [3][64]
     double* ys = xh + 3 * TB;                  // [64] right-hand side of the diagonal block
-    double* d2s = ys + TB;                     // [2][64] distance-2 sums
+    double* base = ys + TB;                    // [2][64]
+    double* d2p = base + 2 * TB;               // [2][64] halves of the distance-2 sum
     const bool crit = w < 4;
     const int ct = crit ? tid : tid - 128;     // thread index within its group of 128
-    const int r = ct >> 1, hh = ct & 1;        // row and half
+    const int r = ct >> 1, hh = ct & 1;        // row and half (critical path)
+    const int q64 = ct & 63, qh = ct >> 6;     // distance-2 layout
     // Term i (0..31) of half hh: the column index of a tile row.  The order
     // keeps a warp's shared-memory reads on distinct banks: T[term * TLD + r]
     // for TRANS 0, T[r * TLD + term] for TRANS 1.
@@ -361,22 +363,58 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
     auto issue_zc1 = [&](int tt) {             // Z_tt and C1_tt
       const int k = chain_block<TRANS>(tt, nblk);
       const double* src = a.Z + (size_t)k * TB * TB;
-      double* dst = Zb + (tt & 1) * TTILE;
+      double* dst = Zb + (tt % 3) * TTILE;
       for (int idx = ct; idx < TB * TB / 2; idx += 128) {
         const int rr = (idx & (TB / 2 - 1)) * 2, cc = idx >> 5;
         cp_async16(dst + cc * TLD + rr, src + cc * TB + rr);
       }
       if (tt >= 1) {
         const int j = chain_block<TRANS>(tt - 1, nblk);
-        if (TRANS == 0) load_tile(C1b + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, ct, 128);
-        else load_tile(C1b + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, ct, 128);
+        if (TRANS == 0) load_tile(C1b + (tt % 3) * TTILE, a.R, a.ldr, n, k, j, ct, 128);
+        else load_tile(C1b + (tt % 3) * TTILE, a.R, a.ldr, n, j, k, ct, 128);
       }
     };
-    auto issue_c2 = [&](int tt) {              // C2_tt
-      if (tt >= 2 && tt < nblk) {
-        const int k = chain_block<TRANS>(tt, nblk), j = chain_block<TRANS>(tt - 2, nblk);
-        if (TRANS == 0) load_tile(C2b + (tt & 1) * TTILE, a.R, a.ldr, n, k, j, ct, 128);
-        else load_tile(C2b + (tt & 1) * TTILE, a.R, a.ldr, n, j, k, ct, 128);
+    // C2_tt in registers, 32 entries a thread along R's columns: TRANS 0 row
+    // q64 of block k, columns 32 qh + i of block j; TRANS 1 row q64 of block
+    // j, columns 32 qh + i of block k.
+    double c2v[32];
+    auto fetch_c2 = [&](int tt) {
+      const int k = chain_block<TRANS>(tt, nblk), j = chain_block<TRANS>(tt - 2, nblk);
+      const int gr = (TRANS == 0 ? k : j) * TB + q64, gc0 = (TRANS == 0 ? j : k) * TB + 32 * qh;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        c2v[i] = (gr < n && gc0 + i < n) ? __ldg(a.R + (size_t)(gc0 + i) * a.ldr + gr) : 0.0;
+    };
+    // halves of C2 x_{t-2} for the step that c2v belongs to, into d2p[2][64]
+    auto dist2 = [&](const double* xv) {
+      if (TRANS == 0) {  // row q64: sum over the columns of half qh
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) {
+          s0 += c2v[i] * xv[32 * qh + i];
+          s1 += c2v[i + 1] * xv[32 * qh + i + 1];
+          s2 += c2v[i + 2] * xv[32 * qh + i + 2];
+          s3 += c2v[i + 3] * xv[32 * qh + i + 3];
+        }
+        d2p[qh * TB + q64] = (s0 + s1) + (s2 + s3);
+      } else {           // column 32 qh + i: sum over this warp's 32 source rows
+        const double xy = xv[q64];
+        double v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = c2v[i] * xy;
+        // reduce-scatter over the lanes: lane L ends with the sum of entry L
+#define RS_STEP(O)                                                   \
+  {                                                                  \
+    const bool up = (lane & (O)) != 0;                               \
+    _Pragma("unroll") for (int i = 0; i < (O); ++i) {                \
+      const double send = up ? v[i] : v[i + (O)];                    \
+      const double keep = up ? v[i + (O)] : v[i];                    \
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, (O));         \
+    }                                                                \
+  }
+        RS_STEP(16) RS_STEP(8) RS_STEP(4) RS_STEP(2) RS_STEP(1)
+#undef RS_STEP
+        d2p[(q64 >> 5) * TB + 32 * qh + lane] = v[0];
       }
     };
     // the terms of Z's row r that can be nonzero, at warp granularity:
@@ -385,41 +423,54 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
     if (!crit) {
       issue_zc1(0);
       cp_async_commit();
-      cp_async_wait0();
-      if (ct < TB) d2s[ct] = 0.0;
+      if (nblk > 1) issue_zc1(1);
+      cp_async_commit();
+      if (ct < TB) {
+        const int r0 = chain_block<TRANS>(0, nblk) * TB;
+        base[ct] = r0 + ct < n ? a.rhs[r0 + ct] : 0.0;
+      }
+      cp_async_wait1();
     }
     __syncthreads();
     for (int t = 0; t < nblk; ++t) {
       if (crit) {
         const int k = chain_block<TRANS>(t, nblk);
         const int r0 = k * TB, rows = min(TB, n - r0);
-        double base = r < rows ? a.rhs[r0 + r] : 0.0;
-        if (t >= CHAIN_NEAR) base -= __ldcg(a.accbuf + (size_t)k * TB + r);
-        base -= d2s[(t & 1) * TB + r];
-        const double p = t >= 1 ? tile_dot(C1b + (t & 1) * TTILE, xh + ((t + 2) % 3) * TB, 0, 32) : 0.0;
-        if (hh == 0) ys[r] = base - p;
+        const double bs = base[(t & 1) * TB + r];
+        const double p = t >= 1 ? tile_dot(C1b + (t % 3) * TTILE, xh + ((t + 2) % 3) * TB, 0, 32) : 0.0;
+        if (hh == 0) ys[r] = bs - p;
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        const double xr = tile_dot(Zb + (t & 1) * TTILE, ys, zi0, zi1);
+        const double xr = tile_dot(Zb + (t % 3) * TTILE, ys, zi0, zi1);
         if (hh == 0) {
           xh[(t % 3) * TB + r] = xr;
           if (r < rows) a.x[r0 + r] = xr;
         }
       } else {
+        const bool more = t + 1 < nblk;
+        const int r1 = more ? chain_block<TRANS>(t + 1, nblk) * TB : 0;
+        const double rb = more && ct < TB && r1 + ct < n ? a.rhs[r1 + ct] : 0.0;
         if (ct == 0 && t >= 1) {  // blocks 0 .. t-1 are in a.x (barrier at the end of step t-1)
           __threadfence();
           st_release(a.prog, (unsigned int)t);
         }
-        if (t + 1 < nblk) issue_zc1(t + 1);
+        if (t + 2 < nblk) issue_zc1(t + 2);
         cp_async_commit();
-        issue_c2(t + 2);
-        cp_async_commit();
-        cp_async_wait2();  // C2_{t+1}, issued one step earlier
-        asm volatile("bar.sync 2, 128;" ::: "memory");
-        if (t + 1 < nblk) {
-          const double p = t + 1 >= 2 ? tile_dot(C2b + ((t + 1) & 1) * TTILE, xh + ((t + 2) % 3) * TB, 0, 32) : 0.0;
-          if (hh == 0) d2s[((t + 1) & 1) * TB + r] = p;
+        if (more) {
+          if (t + 1 >= 2) {
+            dist2(xh + ((t + 2) % 3) * TB);
+          } else if (ct < TB) {
+            d2p[ct] = 0.0;
+            d2p[TB + ct] = 0.0;
+          }
+          if (t + 2 < nblk) fetch_c2(t + 2);
           if (ct == 0 && t + 1 >= CHAIN_NEAR)
             wait_flag(a.accflag + chain_block<TRANS>(t + 1, nblk), epoch, a.err);
+        }
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (more && ct < TB) {
+          double b = rb;
+          if (t + 1 >= CHAIN_NEAR) b -= __ldcg(a.accbuf + (size_t)r1 + ct);
+          base[((t + 1) & 1) * TB + ct] = b - (d2p[ct] + d2p[TB + ct]);
         }
         cp_async_wait1();  // Z_{t+1} and C1_{t+1}
       }
@@ -502,31 +553,33 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
       __syncthreads();
       seen = seen_s;
     }
+    double xv[8], z0 = 0.0, z1 = 0.0;
     if (TRANS == 0) {
-      double xv[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int y = w + 8 * q;
         xv[q] = c0 + y < n ? __ldcg(a.x + c0 + y) : 0.0;
       }
+    } else {
+      z0 = __ldcg(a.x + c0 + lane);
+      z1 = __ldcg(a.x + c0 + lane + 32);
+    }
+    // The target due now (its last helper source) first, then published;
+    // then the targets still live.  Slots past their target (or empty) do no
+    // arithmetic.
 #pragma unroll
-      for (int m = 0; m < HMAXT; ++m)
+    for (int m = 0; m < HMAXT; ++m) {
+      if (!(m < nt && tg[m] == u + CHAIN_NEAR)) continue;
+      if (TRANS == 0) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           pa[m][0] += tv[m][2 * q] * xv[q];
           pa[m][1] += tv[m][2 * q + 1] * xv[q];
         }
-    } else {
-      const double z0 = __ldcg(a.x + c0 + lane), z1 = __ldcg(a.x + c0 + lane + 32);
-#pragma unroll
-      for (int m = 0; m < HMAXT; ++m)
+      } else {
 #pragma unroll
         for (int q = 0; q < 8; ++q) ptp[m][q] += tv[m][2 * q] * z0 + tv[m][2 * q + 1] * z1;
-    }
-    // a target whose last helper source this was: publish its partial sum
-#pragma unroll
-    for (int m = 0; m < HMAXT; ++m) {
-      if (!(m < nt && tg[m] == u + CHAIN_NEAR)) continue;
+      }
       const int k = chain_block<TRANS>(tg[m], nblk);
       double* out = a.accbuf + (size_t)k * TB;
       if (TRANS == 0) {
@@ -543,15 +596,42 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
           __threadfence();
         }
       } else {
+        // sum of ptp[m][q] over the lanes, lane q (< 8) ends with entry q
+        double v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const double v = warp_sum(ptp[m][q]);
-          if (lane == 0) out[w + 8 * q] = v;
+        for (int q = 0; q < 8; ++q) v[q] = ptp[m][q];
+#pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) {
+          const bool up = (lane & o) != 0;
+#pragma unroll
+          for (int q = 0; q < o; ++q) {
+            const double send = up ? v[q] : v[q + o];
+            const double keep = up ? v[q + o] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
         }
+        // lanes L and L ^ 8, L ^ 16, L ^ 24 hold partial sums of entry L & 7
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 8);
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+        if (lane < 8) out[w + 8 * lane] = v[0];
         __threadfence();
       }
       __syncthreads();
       if (tid == 0) st_release(a.accflag + k, epoch);
+    }
+#pragma unroll
+    for (int m = 0; m < HMAXT; ++m) {
+      if (!(m < nt && tg[m] > u + CHAIN_NEAR)) continue;
+      if (TRANS == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          pa[m][0] += tv[m][2 * q] * xv[q];
+          pa[m][1] += tv[m][2 * q + 1] * xv[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ptp[m][q] += tv[m][2 * q] * z0 + tv[m][2 * q + 1] * z1;
+      }
     }
   }
 }
