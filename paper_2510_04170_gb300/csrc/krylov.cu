@@ -233,7 +233,6 @@ __device__ __forceinline__ void cp_async16(double* dst, const double* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Tile of R with row block a and column block b into shared memory,
@@ -296,6 +295,27 @@ __global__ void __launch_bounds__(256) k_trsv_dinv(const double* __restrict__ R,
   }
 }
 
+// A helper's partial sum is published by overwriting this value, which the
+// chain polls for: a signalling NaN with a fixed payload, which no
+// arithmetic result has (operations on NaN return the canonical quiet NaN).
+constexpr unsigned long long ACC_EMPTY = 0x7FF4A5A5A5A5A5A5ull;
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_b64(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Before each chain launch: the progress counter at 0 and every helper
+// partial sum at ACC_EMPTY.
+__global__ void k_trsv_chain_prep(unsigned int* __restrict__ prog, double* __restrict__ accbuf, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *prog = 0u;
+  if (i < count) reinterpret_cast<unsigned long long*>(accbuf)[i] = ACC_EMPTY;
+}
+
 struct ChainArgs {
   const double* R;
   const double* Z;            // inverses of the diagonal blocks (k_trsv_dinv)
@@ -303,10 +323,8 @@ struct ChainArgs {
   int n, nblk, H;
   const double* rhs;
   double* x;
-  double* accbuf;             // [nblk][64] helper partial sums
-  unsigned int* accflag;      // [nblk] epoch when accbuf[k] is complete
-  unsigned int* prog;         // number of blocks the chain has published (reset to 0 by k_trsv_prep)
-  const unsigned int* epoch_dev;
+  double* accbuf;             // [nblk][64] helper partial sums, ACC_EMPTY until published
+  unsigned int* prog;         // number of blocks the chain has published (reset by k_trsv_chain_prep)
   unsigned int* err;
   const int* skip;
 };
@@ -315,9 +333,10 @@ template <int TRANS>
 __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) double csm[];
-  const unsigned int epoch = *a.epoch_dev;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int nblk = a.nblk, n = a.n;
+  const int wlim = (int)__ldcg(a.err + (SYNC_WAITLIM - SYNC_ERR));
+  const unsigned int wlimit = wlim == 0 ? (1u << 22) : (unsigned int)wlim;
   if (blockIdx.x == 0) {
     // ------------------------------------------------------------ chain
     // Warps 0-3 take step t's critical path: y = base_t - C1_t x_{t-1}, then
@@ -449,7 +468,7 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         const bool more = t + 1 < nblk;
         const int r1 = more ? chain_block<TRANS>(t + 1, nblk) * TB : 0;
         const double rb = more && ct < TB && r1 + ct < n ? a.rhs[r1 + ct] : 0.0;
-        if (ct == 0 && t >= 1) {  // blocks 0 .. t-1 are in a.x (barrier at the end of step t-1)
+        if (ct == 96 && t >= 1) {  // blocks 0 .. t-1 are in a.x (barrier at the end of step t-1)
           __threadfence();
           st_release(a.prog, (unsigned int)t);
         }
@@ -463,20 +482,31 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
             d2p[TB + ct] = 0.0;
           }
           if (t + 2 < nblk) fetch_c2(t + 2);
-          if (ct == 0 && t + 1 >= CHAIN_NEAR)
-            wait_flag(a.accflag + chain_block<TRANS>(t + 1, nblk), epoch, a.err);
+        }
+        // the helpers' sum of step t + 1: poll the entry until it is published
+        double acc = 0.0;
+        if (more && ct < TB && t + 1 >= CHAIN_NEAR) {
+          const double* src = a.accbuf + (size_t)r1 + ct;
+          unsigned long long v = ld_relaxed_b64(src);
+          unsigned int spins = 0;
+          while (v == ACC_EMPTY) {
+            if (wlim < 0 || ++spins > wlimit) {
+              atomicExch(a.err, 1u);
+              v = 0ull;
+              break;
+            }
+            if (spins > (1u << 16)) __nanosleep(128);
+            v = ld_relaxed_b64(src);
+          }
+          acc = __longlong_as_double((long long)v);
         }
         asm volatile("bar.sync 2, 128;" ::: "memory");
-        if (more && ct < TB) {
-          double b = rb;
-          if (t + 1 >= CHAIN_NEAR) b -= __ldcg(a.accbuf + (size_t)r1 + ct);
-          base[((t + 1) & 1) * TB + ct] = b - (d2p[ct] + d2p[TB + ct]);
-        }
+        if (more && ct < TB) base[((t + 1) & 1) * TB + ct] = (rb - acc) - (d2p[ct] + d2p[TB + ct]);
         cp_async_wait1();  // Z_{t+1} and C1_{t+1}
       }
       __syncthreads();
     }
-    if (!crit && ct == 0) {
+    if (!crit && ct == 96) {
       __threadfence();
       st_release(a.prog, (unsigned int)nblk);
     }
@@ -505,8 +535,6 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
     for (int q = 0; q < 8; ++q) ptp[m][q] = 0.0;
   }
   unsigned int seen = 0;
-  const int lim = (int)__ldcg(a.err + (SYNC_WAITLIM - SYNC_ERR));
-  const unsigned int limit = lim == 0 ? (1u << 22) : (unsigned int)lim;
   for (int u = 0; u + CHAIN_NEAR <= tmax; ++u) {
     const int j = chain_block<TRANS>(u, nblk);
     const int c0 = j * TB;
@@ -540,7 +568,7 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
       if (tid == 0) {
         unsigned int v = ld_acquire(a.prog), spins = 0;
         while (v < (unsigned int)(u + 1)) {
-          if (lim < 0 || ++spins > limit) {
+          if (wlim < 0 || ++spins > wlimit) {
             atomicExch(a.err, 1u);
             v = (unsigned int)(u + 1);
             break;
@@ -591,9 +619,8 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
             double sm = 0.0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) sm += sred[q * TB + lane + 32 * hh];
-            out[lane + 32 * hh] = sm;
+            st_relaxed_f64(out + lane + 32 * hh, sm);
           }
-          __threadfence();
         }
       } else {
         // sum of ptp[m][q] over the lanes, lane q (< 8) ends with entry q
@@ -613,11 +640,9 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         // lanes L and L ^ 8, L ^ 16, L ^ 24 hold partial sums of entry L & 7
         v[0] += __shfl_xor_sync(0xffffffffu, v[0], 8);
         v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
-        if (lane < 8) out[w + 8 * lane] = v[0];
-        __threadfence();
+        if (lane < 8) st_relaxed_f64(out + w + 8 * lane, v[0]);
       }
-      __syncthreads();
-      if (tid == 0) st_release(a.accflag + k, epoch);
+      __syncthreads();  // sred is rewritten by the next publication
     }
 #pragma unroll
     for (int m = 0; m < HMAXT; ++m) {
@@ -737,18 +762,18 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
     return RFM_EINVAL;
   }
   if (p->dinv && p->dinv_of != p->R) RFM_TRY(rfm_trsv_prepare(p));
-  k_trsv_prep<<<1, 1, 0, p->stream>>>(p->sync + SYNC_EPOCH, p->sync + SYNC_TICKET);
-  RFM_CHECK_LAUNCH();
   ProfScope ps(PF_TRSV, p->stream);
   rfm_prof_work(PF_TRSV, 8.0 * (double)n * (n + 1) / 2 + 16.0 * n);  // R read once, b and x
   // chain + helpers when every target past distance 2 has a helper slot
   const int nsm = rfm_num_sms();
   const int H = nblk > CHAIN_NEAR ? std::min(nsm - 1, nblk - CHAIN_NEAR) : 0;
   if (p->trsv_acc && p->dinv && nsm > 1 && nblk - CHAIN_NEAR <= HMAXT * H) {
+    k_trsv_chain_prep<<<(nblk * TB + 255) / 256, 256, 0, p->stream>>>(p->sync + SYNC_TICKET, p->trsv_acc, nblk * TB);
+    RFM_CHECK_LAUNCH();
     ChainArgs a;
     a.R = p->R; a.Z = p->dinv; a.ldr = p->ldr; a.n = n; a.nblk = nblk; a.H = H; a.rhs = b; a.x = x;
-    a.accbuf = p->trsv_acc; a.accflag = p->sync + SYNC_FLAGS; a.prog = p->sync + SYNC_TICKET;
-    a.epoch_dev = p->sync + SYNC_EPOCH; a.err = p->sync + SYNC_ERR; a.skip = p->skip;
+    a.accbuf = p->trsv_acc; a.prog = p->sync + SYNC_TICKET;
+    a.err = p->sync + SYNC_ERR; a.skip = p->skip;
     const void* fn = trans == 0 ? (const void*)k_trsv_chain<0> : (const void*)k_trsv_chain<1>;
     RFM_CUDA(rfm_smem_attr(fn, (int)chain_smem_bytes()));
     cudaLaunchConfig_t cfg = {};
@@ -766,6 +791,8 @@ rfm_status rfm_launch_trsv(rfm_problem* p, int trans, const double* b, double* x
     RFM_CHECK_LAUNCH();
     return RFM_OK;
   }
+  k_trsv_prep<<<1, 1, 0, p->stream>>>(p->sync + SYNC_EPOCH, p->sync + SYNC_TICKET);
+  RFM_CHECK_LAUNCH();
   if (trans == 0)
     k_trsv<0><<<nblk, 256, 0, p->stream>>>(p->R, p->ldr, n, b, x, p->sync + SYNC_FLAGS, p->sync + SYNC_EPOCH,
                                            p->sync + SYNC_TICKET, p->sync + SYNC_ERR, p->skip);
