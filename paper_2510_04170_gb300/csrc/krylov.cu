@@ -393,52 +393,68 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         else load_tile(C1b + (tt % 3) * TTILE, a.R, a.ldr, n, j, k, ct, 128);
       }
     };
-    // C2_tt in registers, 32 entries a thread along R's columns: TRANS 0 row
-    // q64 of block k, columns 32 qh + i of block j; TRANS 1 row q64 of block
-    // j, columns 32 qh + i of block k.
+    // C2_tt in registers: thread (q64, qh) holds the 32 entries of output
+    // row q64 of block k against the source rows 32 qh .. 32 qh + 31 of
+    // block j.  TRANS 0: R(k*64 + q64, j*64 + 32 qh + i), one column of R per
+    // entry, the lanes of a warp on consecutive rows; TRANS 1 (the coupling
+    // of R^T): R(j*64 + 32 qh + i, k*64 + q64), 32 consecutive entries of one
+    // column of R per thread.
     double c2v[32];
     auto fetch_c2 = [&](int tt) {
       const int k = chain_block<TRANS>(tt, nblk), j = chain_block<TRANS>(tt - 2, nblk);
-      const int gr = (TRANS == 0 ? k : j) * TB + q64, gc0 = (TRANS == 0 ? j : k) * TB + 32 * qh;
+      const int go = k * TB + q64, gs = j * TB + 32 * qh;  // output index, first source index
 #pragma unroll
-      for (int i = 0; i < 32; ++i)
-        c2v[i] = (gr < n && gc0 + i < n) ? __ldg(a.R + (size_t)(gc0 + i) * a.ldr + gr) : 0.0;
-    };
-    // halves of C2 x_{t-2} for the step that c2v belongs to, into d2p[2][64]
-    auto dist2 = [&](const double* xv) {
-      if (TRANS == 0) {  // row q64: sum over the columns of half qh
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll
-        for (int i = 0; i < 32; i += 4) {
-          s0 += c2v[i] * xv[32 * qh + i];
-          s1 += c2v[i + 1] * xv[32 * qh + i + 1];
-          s2 += c2v[i + 2] * xv[32 * qh + i + 2];
-          s3 += c2v[i + 3] * xv[32 * qh + i + 3];
-        }
-        d2p[qh * TB + q64] = (s0 + s1) + (s2 + s3);
-      } else {           // column 32 qh + i: sum over this warp's 32 source rows
-        const double xy = xv[q64];
-        double v[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = c2v[i] * xy;
-        // reduce-scatter over the lanes: lane L ends with the sum of entry L
-#define RS_STEP(O)                                                   \
-  {                                                                  \
-    const bool up = (lane & (O)) != 0;                               \
-    _Pragma("unroll") for (int i = 0; i < (O); ++i) {                \
-      const double send = up ? v[i] : v[i + (O)];                    \
-      const double keep = up ? v[i + (O)] : v[i];                    \
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, (O));         \
-    }                                                                \
-  }
-        RS_STEP(16) RS_STEP(8) RS_STEP(4) RS_STEP(2) RS_STEP(1)
-#undef RS_STEP
-        d2p[(q64 >> 5) * TB + 32 * qh + lane] = v[0];
+      for (int i = 0; i < 32; ++i) {
+        const bool ok = go < n && gs + i < n;
+        if (TRANS == 0) c2v[i] = ok ? __ldg(a.R + (size_t)(gs + i) * a.ldr + go) : 0.0;
+        else c2v[i] = ok ? __ldg(a.R + (size_t)go * a.ldr + gs + i) : 0.0;
       }
     };
-    // the terms of Z's row r that can be nonzero, at warp granularity:
-    // TRANS 0 (upper) columns >= 16 w, TRANS 1 (lower) columns < 16 (w + 1)
-    const int zi0 = TRANS == 0 ? 8 * w : 0, zi1 = TRANS == 0 ? 32 : 8 * (w + 1);
+    // the half qh of C2 x_{t-2} for output q64, into d2p[2][64]
+    auto dist2 = [&](const double* xv) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        s0 += c2v[i] * xv[32 * qh + i];
+        s1 += c2v[i + 1] * xv[32 * qh + i + 1];
+        s2 += c2v[i + 2] * xv[32 * qh + i + 2];
+        s3 += c2v[i + 3] * xv[32 * qh + i + 3];
+      }
+      d2p[qh * TB + q64] = (s0 + s1) + (s2 + s3);
+    };
+    // x = Z y with the triangle balanced over the threads: rows g and 63 - g
+    // share four threads (s = ct & 3), whose terms are the positions p = s,
+    // s + 4, ... of the pair's 65 terms (row A = g first, then row B = 63 - g).
+    const int zg = ct >> 2, zs = ct & 3;
+    const int zA = zg, zB = TB - 1 - zg;
+    const int znA = TRANS == 0 ? TB - zg : zg + 1;  // terms of row A
+    auto zdot = [&](const double* Zt, const double* yv, double& xa, double& xb) {
+      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 17; ++i) {
+        const int pos = zs + 4 * i;
+        if (pos > TB) break;  // 65 terms per pair
+        const bool inA = pos < znA;
+        // column of the term: TRANS 0 row A columns g .. 63, row B 63-g .. 63;
+        // TRANS 1 row A columns 0 .. g, row B 0 .. 63-g
+        const int c = TRANS == 0 ? (inA ? zg + pos : pos - 1) : (inA ? pos : pos - znA);
+        const int row = inA ? zA : zB;
+        const double zv = TRANS == 0 ? Zt[c * TLD + row] : Zt[row * TLD + c];
+        const double prod = zv * yv[c];
+        if (inA) {
+          if (i & 1) a1 += prod; else a0 += prod;
+        } else {
+          if (i & 1) b1 += prod; else b0 += prod;
+        }
+      }
+      double sa = a0 + a1, sb = b0 + b1;
+      sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+      sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+      sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+      sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+      xa = sa;
+      xb = sb;
+    };
     if (!crit) {
       issue_zc1(0);
       cp_async_commit();
@@ -459,10 +475,14 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         const double p = t >= 1 ? tile_dot(C1b + (t % 3) * TTILE, xh + ((t + 2) % 3) * TB, 0, 32) : 0.0;
         if (hh == 0) ys[r] = bs - p;
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        const double xr = tile_dot(Zb + (t % 3) * TTILE, ys, zi0, zi1);
-        if (hh == 0) {
-          xh[(t % 3) * TB + r] = xr;
-          if (r < rows) a.x[r0 + r] = xr;
+        double xa, xb;
+        zdot(Zb + (t % 3) * TTILE, ys, xa, xb);
+        if (zs == 0) {
+          xh[(t % 3) * TB + zA] = xa;
+          if (zA < rows) a.x[r0 + zA] = xa;
+        } else if (zs == 1) {
+          xh[(t % 3) * TB + zB] = xb;
+          if (zB < rows) a.x[r0 + zB] = xb;
         }
       } else {
         const bool more = t + 1 < nblk;
@@ -606,7 +626,7 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ptp[m][q] += tv[m][2 * q] * z0 + tv[m][2 * q + 1] * z1;
+        for (int q = 0; q < 8; ++q) ptp[m][q] = fma(tv[m][2 * q + 1], z1, fma(tv[m][2 * q], z0, ptp[m][q]));
       }
       const int k = chain_block<TRANS>(tg[m], nblk);
       double* out = a.accbuf + (size_t)k * TB;
@@ -655,7 +675,7 @@ __global__ void __launch_bounds__(256, 1) k_trsv_chain(ChainArgs a) {
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ptp[m][q] += tv[m][2 * q] * z0 + tv[m][2 * q + 1] * z1;
+        for (int q = 0; q < 8; ++q) ptp[m][q] = fma(tv[m][2 * q + 1], z1, fma(tv[m][2 * q], z0, ptp[m][q]));
       }
     }
   }

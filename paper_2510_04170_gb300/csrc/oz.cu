@@ -116,15 +116,18 @@ __device__ __forceinline__ uint64_t umma_desc(const void* smem_tile) {
   d |= (uint64_t)2 << 61;                // 128-byte swizzle
   return d;
 }
-// kind::f16 instruction descriptor: bf16 A and B (K-major), f32 accumulate, M=128, N=64.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// kind::f16 instruction descriptor: bf16 A and B (K-major), f32 accumulate,
+// M=128, N = 64 w (w = 1, 2 or 4 consecutive B digit tiles).
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -327,16 +330,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
               if (!ok) break;
               tc_fence_after();
               const uint64_t ad = umma_desc(abuf + (size_t)s * ATILE);
-              for (int q = 0; q < g.pB; ++q) {
-                if (p + q + 2 > g.Lmax) break;
+              // Pairs (p, q) with p + q + 2 <= Lmax.  The B digit tiles q, q+1, ...
+              // are consecutive in shared memory and their levels p+q, p+q+1, ...
+              // are consecutive 64-column TMEM accumulators, so w of them form one
+              // MMA with N = 64 w: one read of the A tile serves w pairs.  Each
+              // level receives its pairs in the same order as one MMA per pair.
+              // A group's levels are all fresh (first write) or all started.
+              const int qmax = min(g.pB - 1, g.Lmax - 2 - p);
+              for (int q = 0; q <= qmax;) {
                 const int l = p + q;
+                int w = 4;
+                while (w > 1) {
+                  const unsigned m = ((1u << w) - 1u) << l;
+                  const unsigned fresh = ~initmask & m;
+                  if (q + w - 1 <= qmax && (fresh == 0u || fresh == m)) break;
+                  w >>= 1;
+                }
                 const uint64_t bd = umma_desc(bbuf + (size_t)(b * MAXD + q) * BTILE);
-                const uint32_t first = (initmask >> l) & 1u ? 1u : 0u;
+                const uint32_t started = (initmask >> l) & 1u;
+                const uint32_t idesc = idesc_n(BN * w);
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
-                  umma_bf16(tmem + (uint32_t)(l * BN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                            (first || kk > 0) ? 1u : 0u);
-                initmask |= 1u << l;
+                  umma_bf16(tmem + (uint32_t)(l * BN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                            (started || kk > 0) ? 1u : 0u);
+                initmask |= ((1u << w) - 1u) << l;
+                q += w;
               }
               umma_commit(&bars->a_empty[s]);
               ++aidx;
