@@ -227,6 +227,18 @@ struct OzArgs {
   unsigned* err;
 };
 
+// Tile order: groups of TGM M-tiles, N-tiles swept inside a group with the
+// group's M-tiles fastest, so the CTAs in flight share a few A tiles (the
+// group's, kept in L2) instead of each N-tile re-reading all of A.
+constexpr int TGM = 16;
+__device__ __forceinline__ void tile_coords(int t, const OzArgs& g, int& mt, int& nt) {
+  const int per = TGM * g.ntiles;
+  const int grp = t / per, in = t - grp * per;
+  const int gsz = min(TGM, g.mtiles - grp * TGM);
+  mt = grp * TGM + in % gsz;
+  nt = in / gsz;
+}
+
 struct __align__(8) OzBars {
   uint64_t a_full[ASTAGES], a_empty[ASTAGES], b_full[2], b_empty[2], acc_full, acc_empty, fin;
   uint32_t tmem_base;
@@ -269,14 +281,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
 
-  // Persistent: tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; M-tiles fastest.
+  // Persistent: tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (tile_coords).
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- producer
       unsigned aidx = 0, kglob = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x) {
-        const int mt = t % g.mtiles, nt = t / g.mtiles;
+        int mt, nt;
+        tile_coords(t, g, mt, nt);
         for (int kt = 0; kt < g.ktiles && ok; ++kt) {
           const int b = kglob & 1;
           const unsigned use_b = kglob >> 1;
@@ -380,7 +393,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     unsigned cglob = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
-      const int mt = t % g.mtiles, nt = t / g.mtiles;
+      int mt, nt;
+      tile_coords(t, g, mt, nt);
       if (g.mode != 0) {  // C is read in the final update: start bringing it into L2 now
         const long long gi = (long long)mt * BM + row;
         if (gi < g.M)
