@@ -23,16 +23,16 @@
 // max|A_i.| max|B_.j|).
 //
 // Kernel layout: persistent, one CTA per SM looping over 128 x 64 output
-// tiles, 10 warps.
+// tiles, 18 warps.
 //   warp 0  producer: cp.async.bulk of pre-tiled digit tiles (16 KB A, 8 KB B)
 //           into shared memory, completion on mbarriers (expect_tx)
 //   warp 1  owns the 512-column TMEM allocation; lane 0 issues tcgen05.mma
-//           (kind::f16, bf16 x bf16 -> f32, M=128, N=64, K=16) for every digit
-//           pair into the TMEM accumulator of its level (64 columns each) and
-//           commits to mbarriers
-//   warps 2-9 epilogue: tcgen05.ld the levels of each chunk, combine them
-//           into two int64 running sums per element (two warps per TMEM
-//           lane quarter, 32 columns each), then round once to FP64, scale
+//           (kind::f16, bf16 x bf16 -> f32, M=128, N=64 w, K=16), one MMA for
+//           w digit pairs that share an A digit, into the TMEM accumulators
+//           of their levels (64 columns each), and commits to mbarriers
+//   warps 2-17 epilogue: tcgen05.ld the levels of each chunk, combine them
+//           into two int64 running sums per element (four warps per TMEM
+//           lane quarter, 16 columns each), then round once to FP64, scale
 //           and write (or subtract from) C; C is prefetched into L2 at the
 //           start of the tile and read-modify-written four columns at a time
 // Digit tiles are K-major with 128-byte rows in the 128B-swizzle pattern so a
@@ -52,7 +52,7 @@ constexpr int ATILE = BM * BK * 2;  // 16384 bytes
 constexpr int BTILE = BN * BK * 2;  // 8192 bytes
 constexpr int MAXD = 8;             // digits per operand
 constexpr int ASTAGES = 6;
-constexpr int EPI_WARPS = 8;        // two warps per TMEM lane quarter, 32 columns each
+constexpr int EPI_WARPS = 16;       // four warps per TMEM lane quarter, 16 columns each
 constexpr int EPI_COLS = BN / (EPI_WARPS / 4);
 constexpr int EPI_GRP = 4;          // C elements loaded per round trip in the final update
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
@@ -149,8 +149,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 
 // Levels l0 .. l0+3 of 8 columns (levels >= nlev read as 0) combined exactly,
 // L_l0 2^(3 BETA) + L_(l0+1) 2^(2 BETA) + L_(l0+2) 2^BETA + L_(l0+3), and
-// added to acc[0..7].  (Ten warps leave 168 registers a thread, which the
-// accumulators mostly fill, so one level is loaded per wait.)
+// added to acc[0..7].  (Eighteen warps leave 96 registers a thread, which the
+// accumulators largely fill, so one level is loaded per wait.)
 __device__ __forceinline__ void tmem_levels4(uint32_t cbase, int l0, int nlev, long long* acc) {
   float v[8];
   long long I[8];
