@@ -211,7 +211,17 @@ def read_dominant(lib, rfm, names, dom_fams):
     return dom_ms, dom_cnt, dom_work
 
 
-def roofline(dom_fams, dom_ms, dom_cnt, dom_work):
+# DRAM traffic per launch of a dominant kernel family, from one ncu capture of
+# the same workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (workload, precision, family).  c2 / 2 / oz_gemm: mean over the first 600 k_oz_gemm
+# launches of one c2 solve (the sketch and the first factorisation; the later
+# factorisations repeat the same shapes), taken with the grouped-MMA,
+# 16-epilogue-warp kernel.  It must be measured again whenever that kernel
+# changes.
+MEASURED_TRAFFIC = {("c2", 2, "oz_gemm"): 12.879e9}
+
+
+def roofline(dom_fams, dom_ms, dom_cnt, dom_work, key=None):
     """Roofline entry of the dominant kernel family from its CUDA-event time,
     launch count and the algorithmic work the library recorded per launch."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -220,7 +230,8 @@ def roofline(dom_fams, dom_ms, dom_cnt, dom_work):
     bound = BOUND.get(dom_fams[0])
     if bound and dom_ms > 0 and dom_work > 0:
         rate = dom_work / (dom_ms / 1e3)
-        common = {"traffic": None, "kernel": "+".join(dom_fams), "launches": dom_cnt,
+        common = {"traffic": MEASURED_TRAFFIC.get(tuple(key or ()) + ("+".join(dom_fams),)), "kernel": "+".join(dom_fams),
+                  "launches": dom_cnt,
                   "avg_launch_ms": dom_ms / max(1, dom_cnt), "work_per_launch": dom_work / max(1, dom_cnt)}
         if bound == "hbm":
             peak = peaks.get("hbm_gbs", 6800.0)
@@ -369,7 +380,7 @@ def run_batch(args, rank, world, local_rank, wl, lib, rfm, dist):
                    "l2": "flushed (512 MiB write) between timed steps"},
         "accuracy": acc,
         "kernel_ms_warmup_step": {k: round(v, 3) for k, v in fam_ms.items() if v > 0},
-        "roofline": roofline(dom_fams, dom_ms, dom_cnt, dom_work),
+        "roofline": roofline(dom_fams, dom_ms, dom_cnt, dom_work, (args.workload, wl["precision"])),
         "gpu_launches": int(launches),
         "e2e": {"value": world * count / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "includes": "batch creation + H2D c0 + solves + D2H c"},
@@ -517,7 +528,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = world / statistics.median(e2e_times) if e2e_times else None
 
     steps_per_rank = args.steps
-    roof = roofline(dom_fams, dom_ms, dom_cnt, dom_work)
+    roof = roofline(dom_fams, dom_ms, dom_cnt, dom_work, (args.workload, wl["precision"]))
     line = {
         "metric": METRIC, "value": value if gate_ok else None, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps,
