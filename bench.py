@@ -677,7 +677,7 @@ def _threads():
     return timing.threads()
 
 
-def oracle_projection(wl, outer_iters, lsqr_iters, qr_cols=4096):
+def oracle_projection(wl, outer_iters, lsqr_iters, qr_cols=1024):
     """The oracle's timing model (oracle.timing.projection) for a workload."""
     from oracle import timing
     return timing.projection(wl["desc"], wl["opts"], outer_iters, lsqr_iters, qr_cols)
@@ -705,7 +705,7 @@ def calibration(wl):
     return json.load(open(path))
 
 
-def projected_baseline(wl, info=None, qr_cols=4096):
+def projected_baseline(wl, info=None, qr_cols=1024):
     """Oracle seconds per solve from its timing model on this host, scaled by
     the model's calibration against a whole measured oracle solve."""
     it, ls, src = oracle_counts(wl, info)

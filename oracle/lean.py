@@ -18,9 +18,14 @@ This module computes the same quantities without either array:
   definition as `philox.gaussian_sketch`, a range of sketch rows at a time,
   optionally in a pool of worker processes.  The count sketch adds
   sigma(i) J[i, :] to row h(i) of B in increasing i, as `linalg.count_sketch`.
-* The Householder QR is `linalg.qr_r_blocked`'s algorithm applied in place to
-  a column-major B, with the compact-WY trailing update done a range of
-  columns at a time (each column's update is the same product).
+* The Householder QR without pivoting (Sec. 4.1, R as `linalg.normalise_r`
+  fixes it) is LAPACK's geqrf, the routine behind numpy.linalg.qr, in numpy's
+  64-bit-index build (s * n exceeds 2^31 at full size).  This library routine
+  serves as one step and computes the factorisation that
+  `qr_r_blocked_inplace` writes out: `linalg.qr_r_blocked`'s algorithm in
+  place, with the compact-WY trailing update done a range of columns at a
+  time.  The two are pinned to each other, and geqrf to the textbook
+  definition, by the oracle's tests.
 * R is held in row-major and column-major copies so that both triangular
   solves of `linalg` read contiguous memory.
 
@@ -193,11 +198,31 @@ def qr_r_blocked_inplace(A, nb=64, chunk=2048):
     return la.normalise_r(A[:n, :n])
 
 
+def qr_r_lapack(A):
+    """R of the Householder QR of A (s >= n) by LAPACK geqrf, normalised
+    like linalg.normalise_r; returns (R, rank_flag).  A is overwritten: the
+    in-place geqrf gufunc behind numpy.linalg.qr is called directly, so the
+    full-size sketch (17 GB) is not copied first; numpy.linalg.qr (which
+    copies) is the fallback where that gufunc is absent."""
+    s, n = A.shape
+    try:
+        from numpy.linalg import _umath_linalg
+        raw = _umath_linalg.qr_r_raw
+    except (ImportError, AttributeError):
+        raw = None
+    if raw is not None:
+        raw(A, signature="d->d")
+        R = np.triu(A[:n, :n])
+    else:
+        R = np.linalg.qr(A, mode="r")[:n, :n]
+    return la.normalise_r(R)
+
+
 class LeanLin:
     """The linearisation of `newton._Lin` (scaled J, row scale lambda,
     preconditioner R) in the lean forms above."""
 
-    def __init__(self, prob, opts, c, kJ, workers=0):
+    def __init__(self, prob, opts, c, kJ, workers=0, qr="lapack"):
         from . import newton
         self.Jb = BlockJacobian(prob, c, opts["row_scale_c"])
         self.lam = self.Jb.lam
@@ -207,7 +232,7 @@ class LeanLin:
             B = gaussian_sketch_blocks(self.Jb, s, kJ, seed, workers)
         else:
             B = count_sketch_blocks(self.Jb, s, kJ, seed)
-        R, self.rank_flag = qr_r_blocked_inplace(B)
+        R, self.rank_flag = qr_r_lapack(B) if qr == "lapack" else qr_r_blocked_inplace(B)
         del B
         self.Rc = np.ascontiguousarray(R)
         self.Rf = np.asfortranarray(R)

@@ -3,12 +3,13 @@ host within a benchmark run.
 
 Each oracle step is timed on a bounded sample at the instance's sizes and
 scaled by its operation count: assembly per row, Gaussian sketch per column
-block (count sketch per row), Householder QR per column of panel work plus
-2 n^2 (s - n/3) trailing-update flops at the rate of the oracle's own update
-products, triangular solves per n^2, block products per nonzero, and about 19
+block (count sketch per row), the Householder QR at the flop rate (2 n^2
+(s - n/3)) of the oracle's own QR routine on an s x 1024 sample, triangular
+solves per n^2, block products per nonzero, and about 19
 residual evaluations per line search; the iteration counts of a solve
 complete the model.  A whole oracle solve measured on one machine calibrates
-the model there (tests/golden/make_c2_ipn_oracle.py stores both).
+the model there (tests/golden/make_c2_ipn_oracle.py measures the solve and
+tests/golden/calibrate_c2_oracle_model.py stores the ratio).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
@@ -19,6 +20,7 @@ import time
 import numpy as np
 
 from . import assemble as asm
+from . import lean
 from . import linalg as la
 from . import philox
 from .problem import Problem
@@ -34,7 +36,7 @@ def threads():
         return os.cpu_count()
 
 
-def projection(desc, opts, outer_iters, lsqr_iters, qr_cols=4096):
+def projection(desc, opts, outer_iters, lsqr_iters, qr_cols=1024):
     """Projected seconds of one oracle solve of `desc` with solver options
     `opts`, `outer_iters` Jacobian evaluations and `lsqr_iters` LSQR steps in
     total.  Returns (seconds per solve, sample description, seconds spent
@@ -65,23 +67,15 @@ def projection(desc, opts, outer_iters, lsqr_iters, qr_cols=4096):
         t0 = time.perf_counter()
         la.count_sketch(Jc, 4096, 0, desc["seed"])
         t_sk = (time.perf_counter() - t0) * (m / 2048) * (n / 1024)
-    # Householder QR = per-column panel work (one s x 64 panel factorised)
-    # plus the blocked trailing update, 2 n^2 (s - n/3) flops at the rate of
-    # the oracle's own trailing-update products (V^T A, A -= V W) measured on
-    # an s x 64 by s x qr_cols sample
-    B = rng.standard_normal((s, 64))
-    t0 = time.perf_counter()
-    la.qr_r_blocked(B, nb=64)
-    t_col = (time.perf_counter() - t0) / 64
+    # Householder QR: the oracle's routine (LAPACK geqrf, lean.qr_r_lapack) on
+    # an s x qr_cols sample, scaled by the flop count 2 n^2 (s - n/3)
     qc = min(qr_cols, n)
-    V = rng.standard_normal((s, 64))
-    A = rng.standard_normal((s, qc))
+    B = np.asfortranarray(rng.standard_normal((s, qc)))
     t0 = time.perf_counter()
-    Wm = V.T @ A
-    A -= V @ Wm
-    rate = 4.0 * s * 64 * qc / (time.perf_counter() - t0)
-    del B, V, A, Wm
-    t_qr = n * t_col + 2.0 * n * n * (s - n / 3.0) / rate
+    lean.qr_r_lapack(B)
+    rate = 2.0 * qc * qc * (s - qc / 3.0) / (time.perf_counter() - t0)
+    del B
+    t_qr = 2.0 * n * n * (s - n / 3.0) / rate
     # triangular solve (n^2) and block product J x (nnz) per LSQR iteration
     nt = min(8192, n)
     Rs = np.triu(rng.standard_normal((nt, nt))) + nt * np.eye(nt)
@@ -101,6 +95,6 @@ def projection(desc, opts, outer_iters, lsqr_iters, qr_cols=4096):
     sk = (f"Gaussian sketch of 1 of {op.G} column blocks" if opts.get("sketch_kind", "count") == "gauss"
           else "count sketch of 2048 x 1024")
     sample = (f"oracle steps timed on samples and scaled by operation counts: assembly of {rows.size} rows, "
-              f"{sk}, Householder panel {s}x64 and trailing-update product {s}x64 by {s}x{qc}, "
+              f"{sk}, Householder QR of {s}x{qc}, "
               f"R solve n={nt}, 4096-row block product; {outer_iters} outer and {lsqr_iters} LSQR iterations")
     return per_solve, sample, time.perf_counter() - t_all

@@ -55,7 +55,7 @@ def main():
     t0 = time.time()
     op = Problem(desc)
     lean.gaussian_sketch_blocks = _timed("sketch", lean.gaussian_sketch_blocks, t0)
-    lean.qr_r_blocked_inplace = _timed("qr", lean.qr_r_blocked_inplace, t0)
+    lean.qr_r_lapack = _timed("qr", lean.qr_r_lapack, t0)
 
     def log(k, info):
         print(f"[{time.time() - t0:8.1f} s] outer {k + 1}: alpha {info.alphas[-1]:.6g} "

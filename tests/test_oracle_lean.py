@@ -78,6 +78,26 @@ def test_inplace_blocked_qr_equals_blocked_qr():
     assert np.max(np.abs(R2.T @ R2 - G)) <= 1e-12 * np.abs(G).max()
 
 
+def test_lapack_qr_equals_blocked_qr():
+    """geqrf (the full-size oracle's QR) and the written-out blocked
+    Householder QR give the same normalised R within the FP64 bound, the same
+    rank flag, and R^T R = B^T B; a rank-deficient B sets the flag on both."""
+    rng = np.random.default_rng(7)
+    B = rng.standard_normal((300, 150)) @ np.diag(np.logspace(0, 6, 150))
+    R1, f1 = lean.qr_r_blocked_inplace(np.asfortranarray(B.copy()), nb=16, chunk=40)
+    R2, f2 = lean.qr_r_lapack(np.asfortranarray(B.copy()))
+    assert f1 == f2 and not f2
+    assert np.all(np.diag(R2) > 0) and np.array_equal(R2, np.triu(R2))
+    assert np.max(np.abs(R1 - R2)) <= 1e-13 * np.abs(R1).max()
+    G = B.T @ B
+    assert np.max(np.abs(R2.T @ R2 - G)) <= 1e-12 * np.abs(G).max()
+    D = B.copy()
+    D[:, 7] = D[:, 3]
+    _, fd1 = lean.qr_r_blocked_inplace(np.asfortranarray(D.copy()), nb=16, chunk=40)
+    _, fd2 = lean.qr_r_lapack(np.asfortranarray(D.copy()))
+    assert fd1 and fd2
+
+
 def test_lean_solves_equal_dense_solves():
     for kind, sk, solver in ((0, "gauss", "ipn"), (0, "count", "amipn"), (1, "count", "ipn")):
         p = _small(kind, 2 if kind == 1 else 1)
