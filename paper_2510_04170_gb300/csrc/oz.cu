@@ -578,11 +578,13 @@ __device__ __forceinline__ void digits_of(double x, int e, int ndig, float* d) {
 // Digit tiles: out[d][rtile][ktile][tile], tile = TR rows x 64 k in the 128B
 // swizzle.  One thread per 16-byte chunk (row r, 8 consecutive k): it reads 8
 // values and writes one 16-byte chunk per digit plane.
+// The tiles go to row-tile positions rt0 .. rt0 + rtiles - 1 of digit planes
+// that hold plane_rtiles row tiles each (several slices can share one operand).
 template <class Acc, int TR>
 __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict__ e, int ndig, long long rtiles,
-                         long long ktiles, uint16_t* __restrict__ out) {
+                         long long ktiles, uint16_t* __restrict__ out, long long plane_rtiles, long long rt0) {
   const long long total = rtiles * TR * ktiles * 8;
-  const size_t plane = (size_t)rtiles * ktiles * TR * 64;  // elements per digit plane
+  const size_t plane = (size_t)plane_rtiles * ktiles * TR * 64;  // elements per digit plane
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int c8 = (int)(t & 7);
@@ -606,7 +608,7 @@ __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict_
         if (d < ndig)
           packed[d][j >> 1] = (__float_as_uint(d0[d]) >> 16) | (__float_as_uint(d1[d]) & 0xFFFF0000u);
     }
-    const size_t base = ((size_t)rt * ktiles + kt) * (TR * 64) + (size_t)(swz128(r, c8 * 8) >> 1);
+    const size_t base = ((size_t)(rt + rt0) * ktiles + kt) * (TR * 64) + (size_t)(swz128(r, c8 * 8) >> 1);
 #pragma unroll
     for (int d = 0; d < MAXD; ++d)
       if (d < ndig)
@@ -628,18 +630,19 @@ long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_row
 
 template <class Acc>
 static rfm_status slice(Acc X, long long R, long long K, int ndig, int tile_rows, int* e, uint16_t* out,
-                        cudaStream_t st) {
+                        cudaStream_t st, long long plane_rtiles = 0, long long rt0 = 0) {
   ProfScope ps(PF_OZ_SLICE, st);
   const int g1 = (int)std::min<long long>((R + 7) / 8, 152LL * 32);
   k_rowexp<<<std::max(1, g1), 256, 0, st>>>(X, R, K, e);
   RFM_CHECK_LAUNCH();
   const long long rt = (R + tile_rows - 1) / tile_rows, kt = (K + 63) / 64;
+  const long long prt = plane_rtiles > 0 ? plane_rtiles : rt;
   const long long total = rt * tile_rows * kt * 8;
   const int g2 = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
   if (tile_rows == BM)
-    k_digits<Acc, BM><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
+    k_digits<Acc, BM><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out, prt, rt0);
   else
-    k_digits<Acc, BN><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out);
+    k_digits<Acc, BN><<<std::max(1, g2), 256, 0, st>>>(X, R, K, e, ndig, rt, kt, out, prt, rt0);
   RFM_CHECK_LAUNCH();
   return RFM_OK;
 }
@@ -651,6 +654,16 @@ rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, 
 rfm_status rfm_oz_slice_house_vt(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
                                  int* e, uint16_t* out, cudaStream_t st) {
   return slice(AccHouseVt{A, lda, j0}, nb, K, ndig, BM, e, out, st);
+}
+rfm_status rfm_oz_slice_strided_at(const double* base, long long si, long long sk, long long R, long long K, int ndig,
+                                   int tile_rows, int* e, uint16_t* out, long long plane_rtiles, long long rt0,
+                                   cudaStream_t st) {
+  return slice(AccStrided{base, si, sk}, R, K, ndig, tile_rows, e, out, st, plane_rtiles, rt0);
+}
+rfm_status rfm_oz_slice_house_vt_at(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
+                                    int tile_rows, int* e, uint16_t* out, long long plane_rtiles, long long rt0,
+                                    cudaStream_t st) {
+  return slice(AccHouseVt{A, lda, j0}, nb, K, ndig, tile_rows, e, out, st, plane_rtiles, rt0);
 }
 rfm_status rfm_oz_slice_house_v(const double* A, long long lda, long long j0, long long rows, long long nb, int ndig,
                                 int* e, uint16_t* out, cudaStream_t st) {

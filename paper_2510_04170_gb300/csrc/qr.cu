@@ -382,8 +382,6 @@ struct QrScratch {
   double* dg;
 };
 
-int g_panel_occ = 0;
-
 }  // namespace
 
 long long rfm_householder_scratch(long long s, long long n) {
@@ -627,68 +625,27 @@ extern "C" rfm_status rfm_householder_r_noalloc(double* A_dev, int64_t s, int64_
 // diagonal) then update the trailing matrix in compact-WY form
 //     W = V^T A_t,  W2 = T^T W,  A_t -= V W2
 // with both products on the emulated-FP64 tensor-core GEMM (digit splitting,
-// exact level accumulation).  T (128 x 128) comes from the FP64 Gram V^T V and
-// the reflector coefficients, T_jj = tau_j, T_{:j,j} = -tau_j T_{:j,:j} G_{:j,j}.
+// exact level accumulation).  T (128 x 128) comes from the Gram V^T V, which
+// the first product returns next to W, and the reflector coefficients,
+// T_jj = tau_j, T_{:j,j} = -tau_j T_{:j,:j} G_{:j,j}.
 
 rfm_status rfm_oz_slice_house_vt(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
                                  int* e, uint16_t* out, cudaStream_t st);
 rfm_status rfm_oz_slice_house_v(const double* A, long long lda, long long j0, long long rows, long long nb, int ndig,
                                 int* e, uint16_t* out, cudaStream_t st);
+// Digit slices written into row tiles rt0 .. of planes holding plane_rtiles row
+// tiles each, so that several slices form one GEMM operand.
+rfm_status rfm_oz_slice_strided_at(const double* base, long long si, long long sk, long long R, long long K, int ndig,
+                                   int tile_rows, int* e, uint16_t* out, long long plane_rtiles, long long rt0,
+                                   cudaStream_t st);
+rfm_status rfm_oz_slice_house_vt_at(const double* A, long long lda, long long j0, long long nb, long long K, int ndig,
+                                    int tile_rows, int* e, uint16_t* out, long long plane_rtiles, long long rt0,
+                                    cudaStream_t st);
 
 namespace {
 
 constexpr int QB = 128;
 constexpr int QDIG = 8;
-
-// Partial Gram of the block's reflectors over a slice of rows:
-// Gp[z][p][q] = sum_{r in slice z} v_p(r) v_q(r), p <= q.  256 threads, 8x8 each.
-__global__ void __launch_bounds__(256) k_gram_block(const double* __restrict__ A, long long lda, long long s,
-                                                    long long j0, int nbw, long long rchunk, double* __restrict__ Gp) {
-  __shared__ double Vs[32][QB + 1];
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const long long rb = j0 + (long long)blockIdx.x * rchunk;
-  const long long re = min(s, rb + rchunk);
-  double acc[8][8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
-  for (long long r0 = rb; r0 < re; r0 += 32) {
-    for (int idx = tid; idx < 32 * QB; idx += 256) {
-      const int rr = idx & 31, p = idx >> 5;
-      const long long gr = r0 + rr;
-      Vs[rr][p] = (gr < re && p < nbw) ? vval(A, lda, j0, p, gr) : 0.0;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < 32; ++rr) {
-      double a[8], b[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        a[i] = Vs[rr][ty + 16 * i];
-        b[i] = Vs[rr][tx + 16 * i];
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
-    }
-    __syncthreads();
-  }
-  double* out = Gp + (size_t)blockIdx.x * QB * QB;
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) out[(ty + 16 * i) * QB + tx + 16 * j] = acc[i][j];
-}
-
-// G = sum_z Gp[z] in a fixed order.
-__global__ void k_block_gsum(const double* __restrict__ Gp, int nz, double* __restrict__ G) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= QB * QB) return;
-  double s = 0.0;
-  for (int z = 0; z < nz; ++z) s += Gp[(size_t)z * QB * QB + idx];
-  G[idx] = s;
-}
 
 // T from G and tau, column by column.  One CTA of QB threads; T is kept in
 // dynamic shared memory (QB x (QB+1) doubles).
@@ -731,14 +688,13 @@ __global__ void k_block_wt(const double* __restrict__ T, const double* __restric
 }  // namespace
 
 long long rfm_householder_emulated_bytes(long long s, long long n) {
-  const long long nzg = 152;
   long long b = 0;
   b += rfm_oz_digit_bytes(QB, s, QDIG, 128);  // V^T
-  b += rfm_oz_digit_bytes(n, s, QDIG, 64);    // A_t
+  b += rfm_oz_digit_bytes(n + QB, s, QDIG, 64);  // [V, A_t]: the Gram and V^T A_t in one product
   b += rfm_oz_digit_bytes(s, QB, QDIG, 128);  // V
   b += rfm_oz_digit_bytes(n, QB, QDIG, 64);   // W2
-  b += 8LL * (2LL * QB * n + nzg * QB * QB + 3LL * QB * QB);
-  b += 4LL * (QB + n + s + n) + 4096;
+  b += 8LL * (2LL * QB * (n + QB) + 3LL * QB * QB);
+  b += 4LL * (QB + n + QB + s + n) + 4096;
   return b;
 }
 
@@ -767,16 +723,15 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
     return r;
   };
   uint16_t* d_vt = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(QB, s, QDIG, 128)));
-  uint16_t* d_at = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(n, s, QDIG, 64)));
+  uint16_t* d_at = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(n + QB, s, QDIG, 64)));
   uint16_t* d_v = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(s, QB, QDIG, 128)));
   uint16_t* d_w2 = reinterpret_cast<uint16_t*>(take(rfm_oz_digit_bytes(n, QB, QDIG, 64)));
-  double* Wm = reinterpret_cast<double*>(take(8LL * QB * n));
+  double* Wm = reinterpret_cast<double*>(take(8LL * QB * (n + QB)));  // [G, W] = V^T [V, A_t]
   double* W2 = reinterpret_cast<double*>(take(8LL * QB * n));
-  double* Gp = reinterpret_cast<double*>(take(8LL * 152 * QB * QB));
   double* T = reinterpret_cast<double*>(take(8LL * QB * QB));
-  double* Gs = reinterpret_cast<double*>(take(8LL * QB * QB));
+  (void)take(8LL * QB * QB);
   int* e_vt = reinterpret_cast<int*>(take(4LL * QB));
-  int* e_at = reinterpret_cast<int*>(take(4LL * n));
+  int* e_at = reinterpret_cast<int*>(take(4LL * (n + QB)));
   int* e_v = reinterpret_cast<int*>(take(4LL * s));
   int* e_w2 = reinterpret_cast<int*>(take(4LL * n));
   unsigned int* err = sync + SYNC_ERR;
@@ -790,23 +745,21 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
     RFM_TRY(factor_range(A, s, lda, J0, c1, c1, st, q, sync, panel_cap));
     if (nt <= 0) break;
     {
-      ProfScope ps(PF_QR_PANEL, st);
-      const long long nzg = std::min<long long>(152, (rows + 255) / 256);
-      const long long rchunk = (rows + nzg - 1) / nzg;
-      const long long nz = (rows + rchunk - 1) / rchunk;
-      k_gram_block<<<(unsigned)nz, 256, 0, st>>>(A, lda, s, J0, nbw, rchunk, Gp);
-      RFM_CHECK_LAUNCH();
-      k_block_gsum<<<(QB * QB + 255) / 256, 256, 0, st>>>(Gp, (int)nz, Gs);
-      RFM_CHECK_LAUNCH();
-      k_block_t<<<1, QB, QB * (QB + 1) * sizeof(double), st>>>(Gs, q.tau + J0, nbw, T);
-      RFM_CHECK_LAUNCH();
-    }
-    {
+      // One emulated product gives the block's Gram and V^T A_t: its B operand
+      // is [V, A_t] (V^T as the first two 64-row tiles, then the trailing
+      // columns), so C = [G, W] with G = V^T V (exactly symmetric: the digit
+      // pairs (p, q) and (q, p) give the same integer level sums).  T then
+      // comes from G and tau, T_jj = tau_j, T_{:j,j} = -tau_j T_{:j,:j} G_{:j,j}.
       ProfScope ps(PF_QR_VTA, st);
+      const long long prt = 2 + (nt + 63) / 64;  // row tiles of the B operand
       RFM_TRY(rfm_oz_slice_house_vt(A, lda, J0, nbw, rows, QDIG, e_vt, d_vt, st));
-      RFM_TRY(rfm_oz_slice_strided(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, e_at, d_at, st));
-      RFM_TRY(rfm_oz_gemm(d_vt, QDIG, e_vt, d_at, QDIG, e_at, nbw, nt, rows, QDIG + 1, Wm, QB, 0, err, st));
-      k_block_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(T, Wm, nbw, nt, W2);
+      RFM_TRY(rfm_oz_slice_house_vt_at(A, lda, J0, nbw, rows, QDIG, 64, e_at, d_at, prt, 0, st));
+      RFM_TRY(rfm_oz_slice_strided_at(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, e_at + QB, d_at, prt, 2,
+                                      st));
+      RFM_TRY(rfm_oz_gemm(d_vt, QDIG, e_vt, d_at, QDIG, e_at, nbw, QB + nt, rows, QDIG + 1, Wm, QB, 0, err, st));
+      k_block_t<<<1, QB, QB * (QB + 1) * sizeof(double), st>>>(Wm, q.tau + J0, nbw, T);
+      RFM_CHECK_LAUNCH();
+      k_block_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(T, Wm + (size_t)QB * QB, nbw, nt, W2);
       RFM_CHECK_LAUNCH();
     }
     {
