@@ -548,7 +548,7 @@ __global__ void k_rowexp(Acc X, long long R, long long K, int* __restrict__ e) {
 // plain 7-bit field (digit + 64) of U = V + bias, so each digit is one field
 // extract, and the top digit is U >> 7(ndig-1) (the same digits as peeling
 // V from its low end with nearest remainders).
-__device__ __forceinline__ void digits_of(double x, int e, int ndig, float* d) {
+__device__ __forceinline__ long long biased_of(double x, int e, int ndig) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
   unsigned long long m = b & ((1ull << 52) - 1);
@@ -561,18 +561,24 @@ __device__ __forceinline__ void digits_of(double x, int e, int ndig, float* d) {
   if (b >> 63) V = -V;
   // bias = 64 (128^(ndig-1) - 1) / 127: ndig-1 seven-bit fields of value 64
   const long long bias = (long long)(0x0001020408102040ull >> (7 * (MAXD - ndig)));
-  const long long U = V + bias;
-  const unsigned lo = (unsigned)U, hi = (unsigned)((unsigned long long)U >> 32);
-#pragma unroll
-  for (int dd = 1; dd < MAXD; ++dd) {  // plane dd holds bits 7 (ndig-1-dd) .. +6 of U (registers, not stack)
-    if (dd < ndig) {
-      const int bit = 7 * (ndig - 1 - dd);
-      const unsigned f = (bit < 32 ? __funnelshift_r(lo, hi, bit) : hi >> (bit - 32)) & 127u;
-      // exact float of f - 64: 2^23 + f minus (2^23 + 64)
-      d[dd] = __int_as_float((int)(0x4B000000u | f)) - 8388672.0f;
-    }
+  return V + bias;
+}
+
+// bf16 bits of digit dd (0 = the top one) of the biased integer U: the top
+// digit is U >> 7(ndig-1) (|d_1| <= 128), digit dd >= 1 the 7-bit field
+// 7(ndig-1-dd) of U minus 64; small integers, exact in bf16.
+__device__ __forceinline__ uint32_t digit_bits(long long U, int dd, int ndig) {
+  float v;
+  if (dd == 0) {
+    v = (float)(int)(U >> (7 * (ndig - 1)));
+  } else {
+    const int bit = 7 * (ndig - 1 - dd);
+    const unsigned lo = (unsigned)U, hi = (unsigned)((unsigned long long)U >> 32);
+    const unsigned f = (bit < 32 ? __funnelshift_r(lo, hi, bit) : hi >> (bit - 32)) & 127u;
+    // exact float of f - 64: 2^23 + f minus (2^23 + 64)
+    v = __int_as_float((int)(0x4B000000u | f)) - 8388672.0f;
   }
-  d[0] = (float)(int)(U >> (7 * (ndig - 1)));
+  return __float_as_uint(v) >> 16;
 }
 
 // Digit tiles: out[d][rtile][ktile][tile], tile = TR rows x 64 k in the 128B
@@ -594,26 +600,21 @@ __global__ void k_digits(Acc X, long long R, long long K, const int* __restrict_
     const long long kt = rest % ktiles;
     const long long rt = rest / ktiles;
     const long long i = rt * TR + r, k0 = kt * 64 + c8 * 8;
-    uint32_t packed[MAXD][4];
+    // the 8 values' biased integers first, then one digit plane at a time
+    // (few registers: no digits are held for all planes at once)
+    long long U[8];
     const int ei = i < R ? e[i] : 0;
 #pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      float d0[MAXD], d1[MAXD];
-      const double x0 = (i < R && k0 + j < K) ? X(i, k0 + j) : 0.0;
-      const double x1 = (i < R && k0 + j + 1 < K) ? X(i, k0 + j + 1) : 0.0;
-      digits_of(x0, ei, ndig, d0);
-      digits_of(x1, ei, ndig, d1);
-#pragma unroll
-      for (int d = 0; d < MAXD; ++d)
-        if (d < ndig)
-          packed[d][j >> 1] = (__float_as_uint(d0[d]) >> 16) | (__float_as_uint(d1[d]) & 0xFFFF0000u);
-    }
+    for (int j = 0; j < 8; ++j) U[j] = biased_of((i < R && k0 + j < K) ? X(i, k0 + j) : 0.0, ei, ndig);
     const size_t base = ((size_t)(rt + rt0) * ktiles + kt) * (TR * 64) + (size_t)(swz128(r, c8 * 8) >> 1);
 #pragma unroll
     for (int d = 0; d < MAXD; ++d)
       if (d < ndig)
         *reinterpret_cast<uint4*>(out + (size_t)d * plane + base) =
-            make_uint4(packed[d][0], packed[d][1], packed[d][2], packed[d][3]);
+            make_uint4(digit_bits(U[0], d, ndig) | (digit_bits(U[1], d, ndig) << 16),
+                       digit_bits(U[2], d, ndig) | (digit_bits(U[3], d, ndig) << 16),
+                       digit_bits(U[4], d, ndig) | (digit_bits(U[5], d, ndig) << 16),
+                       digit_bits(U[6], d, ndig) | (digit_bits(U[7], d, ndig) << 16));
   }
 }
 
