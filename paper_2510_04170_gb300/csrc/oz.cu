@@ -225,13 +225,20 @@ struct OzArgs {
   long long ldc, M, N;
   int mode;           // 0: C = AB, 1: C -= AB
   unsigned* err;
+  // split K (mode 0): tile t covers the chunks [kz cps, (kz+1) cps) of its
+  // output tile, kz = t mod ksplit, and writes its FP64 partial to
+  // part[kz][i + j M] (summed in order by k_split_sum)
+  int ksplit, cps;
+  double* part;
 };
 
 // Tile order: groups of TGM M-tiles, N-tiles swept inside a group with the
 // group's M-tiles fastest, so the CTAs in flight share a few A tiles (the
 // group's, kept in L2) instead of each N-tile re-reading all of A.
 constexpr int TGM = 16;
-__device__ __forceinline__ void tile_coords(int t, const OzArgs& g, int& mt, int& nt) {
+__device__ __forceinline__ void tile_coords(int t, const OzArgs& g, int& mt, int& nt, int& kz) {
+  kz = t % g.ksplit;
+  t /= g.ksplit;
   const int per = TGM * g.ntiles;
   const int grp = t / per, in = t - grp * per;
   const int gsz = min(TGM, g.mtiles - grp * TGM);
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nlev = min(g.Lmax - 1, g.pA + g.pB - 1);
   const int nchunks = (g.ktiles + KCHUNK - 1) / KCHUNK;
-  const int ntiles_total = g.mtiles * g.ntiles;
+  const int ntiles_total = g.mtiles * g.ntiles * g.ksplit;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ASTAGES; ++s) {
@@ -288,9 +295,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
       unsigned aidx = 0, kglob = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x) {
-        int mt, nt;
-        tile_coords(t, g, mt, nt);
-        for (int kt = 0; kt < g.ktiles && ok; ++kt) {
+        int mt, nt, kz;
+        tile_coords(t, g, mt, nt, kz);
+        const int kt1 = min(g.ktiles, (kz + 1) * g.cps * KCHUNK);
+        for (int kt = kz * g.cps * KCHUNK; kt < kt1 && ok; ++kt) {
           const int b = kglob & 1;
           const unsigned use_b = kglob >> 1;
           if (use_b > 0) ok = mbar_wait(&bars->b_empty[b], (use_b - 1) & 1, g.err, 2);
@@ -325,7 +333,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
       unsigned aidx = 0, kglob = 0, cglob = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x) {
-        for (int c = 0; c < nchunks && ok; ++c) {
+        const int kz = t % g.ksplit;
+        const int c1 = min(nchunks, (kz + 1) * g.cps);
+        for (int c = kz * g.cps; c < c1 && ok; ++c) {
           if (cglob > 0) {
             ok = mbar_wait(&bars->acc_empty, (cglob - 1) & 1, g.err, 6);
             tc_fence_after();
@@ -393,8 +403,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
     unsigned cglob = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles_total && alive; t += gridDim.x) {
-      int mt, nt;
-      tile_coords(t, g, mt, nt);
+      int mt, nt, kz;
+      tile_coords(t, g, mt, nt, kz);
       if (g.mode != 0) {  // C is read in the final update: start bringing it into L2 now
         const long long gi = (long long)mt * BM + row;
         if (gi < g.M)
@@ -411,7 +421,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
         ai[j] = 0;
         al[j] = 0;
       }
-      for (int c = 0; c < nchunks; ++c) {
+      const int c1 = min(nchunks, (kz + 1) * g.cps);
+      for (int c = kz * g.cps; c < c1; ++c) {
         const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, cglob & 1, g.err, 9));
         tc_fence_after();
         if (!ok) {
@@ -457,7 +468,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_oz_gemm(OzArgs g) {
             if (gj < g.N) {
               // value = 2^(e+f-9 BETA) (ai 2^(4 BETA) + al), one rounding to FP64
               const double val = fix_to_double(ai[j0 + i], al[j0 + i], ei + eb[i] - 9 * BETA);
-              g.C[gi + gj * g.ldc] = g.mode == 0 ? val : cv[i] - val;
+              if (g.ksplit > 1) g.part[(size_t)kz * g.M * g.N + gi + gj * g.M] = val;
+              else g.C[gi + gj * g.ldc] = g.mode == 0 ? val : cv[i] - val;
             }
           }
         }
@@ -676,9 +688,30 @@ rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* ro
   return slice(AccJBlock{Jp, Js, rows, m_int, W}, W, K, ndig, BN, e, out, st);
 }
 
+namespace {
+// C[i + j ldc] = sum over z = 0 .. Z-1, in that order, of part[z][i + j M]
+__global__ void k_split_sum(const double* __restrict__ part, int Z, long long M, long long N, double* __restrict__ C,
+                            long long ldc) {
+  const long long MN = M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < MN;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double v = part[idx];
+    for (int z = 1; z < Z; ++z) v += part[(size_t)z * MN + idx];
+    const long long i = idx % M, j = idx / M;
+    C[i + j * ldc] = v;
+  }
+}
+}  // namespace
+
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
                        unsigned* err, cudaStream_t st) {
+  return rfm_oz_gemm_part(Ad, pA, ea, Bd, pB, eb, M, N, K, Lmax, C, ldc, mode, err, st, nullptr, 0);
+}
+
+rfm_status rfm_oz_gemm_part(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
+                            long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
+                            unsigned* err, cudaStream_t st, double* part, long long part_elems) {
   if (pA < 1 || pB < 1 || pA > MAXD || pB > MAXD || Lmax < 2 || Lmax - 1 > 8) {
     rfm_set_error("oz_gemm: bad digit counts");
     return RFM_EINVAL;
@@ -705,8 +738,36 @@ rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t
     return RFM_ECUDA;
   }
   const long long tiles = (long long)a.mtiles * a.ntiles;
-  k_oz_gemm<<<(unsigned)std::min<long long>(tiles, nsm), NTHREADS, oz_smem_bytes(), st>>>(a);
+  // Split K when the output tiles leave the last wave of CTAs partly idle
+  // (mode 0, a workspace for the partials, at least two 512-deep chunks per
+  // split): the split count with the best fill of whole waves, ties to fewer.
+  const int nchunks = (a.ktiles + KCHUNK - 1) / KCHUNK;
+  a.ksplit = 1;
+  a.cps = nchunks;
+  a.part = part;
+  if (mode == 0 && part && tiles < 4LL * nsm && nchunks >= 4) {
+    double best = (double)tiles / (double)(nsm * ((tiles + nsm - 1) / nsm));
+    for (int z = 2; z <= 8 && nchunks / z >= 2; ++z) {
+      const int cps = (nchunks + z - 1) / z;
+      const int zz = (nchunks + cps - 1) / cps;  // no empty split
+      if ((long long)zz * M * N > part_elems) break;
+      const long long u = tiles * zz;
+      const double fill = (double)u / (double)(nsm * ((u + nsm - 1) / nsm));
+      if (fill > best + 0.02) {
+        best = fill;
+        a.ksplit = zz;
+        a.cps = cps;
+      }
+    }
+  }
+  k_oz_gemm<<<(unsigned)std::min<long long>(tiles * a.ksplit, nsm), NTHREADS, oz_smem_bytes(), st>>>(a);
   RFM_CHECK_LAUNCH();
+  if (a.ksplit > 1) {
+    const long long MN = M * N;
+    k_split_sum<<<(unsigned)std::min<long long>((MN + 255) / 256, 152LL * 16), 256, 0, st>>>(part, a.ksplit, M, N, C,
+                                                                                            ldc);
+    RFM_CHECK_LAUNCH();
+  }
   return RFM_OK;
 }
 

@@ -694,6 +694,7 @@ long long rfm_householder_emulated_bytes(long long s, long long n) {
   b += rfm_oz_digit_bytes(s, QB, QDIG, 128);  // V
   b += rfm_oz_digit_bytes(n, QB, QDIG, 64);   // W2
   b += 8LL * (2LL * QB * (n + QB) + 3LL * QB * QB);
+  b += 8LL * 8 * QB * (n + QB);  // split-K partials of V^T [V, A_t]
   b += 4LL * (QB + n + QB + s + n) + 4096;
   return b;
 }
@@ -729,6 +730,8 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
   double* Wm = reinterpret_cast<double*>(take(8LL * QB * (n + QB)));  // [G, W] = V^T [V, A_t]
   double* W2 = reinterpret_cast<double*>(take(8LL * QB * n));
   double* T = reinterpret_cast<double*>(take(8LL * QB * QB));
+  const long long part_elems = 8LL * QB * (n + QB);
+  double* part = reinterpret_cast<double*>(take(8LL * part_elems));
   (void)take(8LL * QB * QB);
   int* e_vt = reinterpret_cast<int*>(take(4LL * QB));
   int* e_at = reinterpret_cast<int*>(take(4LL * (n + QB)));
@@ -756,7 +759,8 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
       RFM_TRY(rfm_oz_slice_house_vt_at(A, lda, J0, nbw, rows, QDIG, 64, e_at, d_at, prt, 0, st));
       RFM_TRY(rfm_oz_slice_strided_at(A + (size_t)c1 * lda + J0, lda, 1, nt, rows, QDIG, 64, e_at + QB, d_at, prt, 2,
                                       st));
-      RFM_TRY(rfm_oz_gemm(d_vt, QDIG, e_vt, d_at, QDIG, e_at, nbw, QB + nt, rows, QDIG + 1, Wm, QB, 0, err, st));
+      RFM_TRY(rfm_oz_gemm_part(d_vt, QDIG, e_vt, d_at, QDIG, e_at, nbw, QB + nt, rows, QDIG + 1, Wm, QB, 0, err, st,
+                               part, part_elems));
       k_block_t<<<1, QB, QB * (QB + 1) * sizeof(double), st>>>(Wm, q.tau + J0, nbw, T);
       RFM_CHECK_LAUNCH();
       k_block_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(T, Wm + (size_t)QB * QB, nbw, nt, W2);

@@ -185,6 +185,13 @@ rfm_status rfm_oz_slice_jblock(const double* Jp, const double* Js, const int* ro
 rfm_status rfm_oz_gemm(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
                        long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
                        unsigned* err, cudaStream_t st);
+// rfm_oz_gemm that may split K over several CTAs per output tile (mode 0,
+// when the tiles alone leave the last wave of CTAs partly idle): the partial
+// products go to part (part_elems doubles; up to 8 M N) and are summed in a
+// fixed order into C.  part = nullptr never splits.
+rfm_status rfm_oz_gemm_part(const uint16_t* Ad, int pA, const int* ea, const uint16_t* Bd, int pB, const int* eb,
+                            long long M, long long N, long long K, int Lmax, double* C, long long ldc, int mode,
+                            unsigned* err, cudaStream_t st, double* part, long long part_elems);
 rfm_status rfm_oz_slice_strided(const double* base, long long si, long long sk, long long R, long long K, int ndig,
                                 int tile_rows, int* e, uint16_t* out, cudaStream_t st);
 long long rfm_oz_digit_bytes(long long rows, long long K, int ndig, int tile_rows);
