@@ -216,9 +216,9 @@ def read_dominant(lib, rfm, names, dom_fams):
 # (workload, precision, family).  c2 / 2 / oz_gemm: mean over the first 600 k_oz_gemm
 # launches of one c2 solve (the sketch and the first factorisation; the later
 # factorisations repeat the same shapes), taken with the grouped-MMA,
-# 16-epilogue-warp kernel.  It must be measured again whenever that kernel
-# changes.
-MEASURED_TRAFFIC = {}
+# 16-epilogue-warp, split-K kernel.  It must be measured again whenever that
+# kernel changes.
+MEASURED_TRAFFIC = {("c2", 2, "oz_gemm"): 13.315e9}
 
 
 def roofline(dom_fams, dom_ms, dom_cnt, dom_work, key=None):
