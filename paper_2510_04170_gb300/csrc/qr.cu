@@ -670,20 +670,6 @@ __global__ void k_block_t(const double* __restrict__ G, const double* __restrict
   for (int idx = threadIdx.x; idx < QB * QB; idx += blockDim.x) T[idx] = Ts[(idx / QB) * (QB + 1) + idx % QB];
 }
 
-// W2[p + c*QB] = sum_{q <= p} T[q][p] W[q + c*QB]
-__global__ void k_block_wt(const double* __restrict__ T, const double* __restrict__ Wm, int nbw, long long nt,
-                           double* __restrict__ W2) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= nt) return;
-  const double* w = Wm + (size_t)c * QB;
-  double* o = W2 + (size_t)c * QB;
-  for (int p = 0; p < QB; ++p) {
-    double s = 0.0;
-    if (p < nbw)
-      for (int q = 0; q <= p; ++q) s += __ldg(T + q * QB + p) * w[q];  // T reads are warp-uniform
-    o[p] = s;
-  }
-}
 
 }  // namespace
 
@@ -763,8 +749,12 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
                                part, part_elems));
       k_block_t<<<1, QB, QB * (QB + 1) * sizeof(double), st>>>(Wm, q.tau + J0, nbw, T);
       RFM_CHECK_LAUNCH();
-      k_block_wt<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(T, Wm + (size_t)QB * QB, nbw, nt, W2);
-      RFM_CHECK_LAUNCH();
+      // W2 = T^T W on the emulated GEMM as well (M = K = 128, N = nt): the
+      // digit buffers of V^T and of W2 are free at this point of the stream.
+      // T is stored row-major, T(q, p) = T[q QB + p], so T^T(p, q) = T[p + q QB].
+      RFM_TRY(rfm_oz_slice_strided(T, 1, QB, nbw, nbw, QDIG, 128, e_vt, d_vt, st));
+      RFM_TRY(rfm_oz_slice_strided(Wm + (size_t)QB * QB, QB, 1, nt, nbw, QDIG, 64, e_w2, d_w2, st));
+      RFM_TRY(rfm_oz_gemm(d_vt, QDIG, e_vt, d_w2, QDIG, e_w2, nbw, nt, nbw, QDIG + 1, W2, QB, 0, err, st));
     }
     {
       ProfScope ps(PF_QR_UPDATE, st);
