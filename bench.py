@@ -213,12 +213,13 @@ def read_dominant(lib, rfm, names, dom_fams):
 
 # DRAM traffic per launch of a dominant kernel family, from one ncu capture of
 # the same workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
-# (workload, precision, family).  c2 / 2 / oz_gemm: mean over the first 600 k_oz_gemm
-# launches of one c2 solve (the sketch and the first factorisation; the later
-# factorisations repeat the same shapes), taken with the grouped-MMA,
-# 16-epilogue-warp, split-K kernel.  It must be measured again whenever that
-# kernel changes.
-MEASURED_TRAFFIC = {}
+# (workload, precision, family).  c2 / 2 / oz_gemm: the first 600 k_oz_gemm
+# launches of one c2 solve (the sketch and the larger early blocks of the
+# first factorisation) moved 1,869 GB/s of their device time. That rate times
+# the solve's mean launch duration (5.17 ms) gives the mean launch's bytes.
+# Taken with the grouped-MMA, 16-epilogue-warp, split-K kernel and the T^T W
+# product; it must be measured again whenever those launches change.
+MEASURED_TRAFFIC = {("c2", 2, "oz_gemm"): 9.66e9}
 
 
 def roofline(dom_fams, dom_ms, dom_cnt, dom_work, key=None):
