@@ -679,7 +679,7 @@ long long rfm_householder_emulated_bytes(long long s, long long n) {
   b += rfm_oz_digit_bytes(n + QB, s, QDIG, 64);  // [V, A_t]: the Gram and V^T A_t in one product
   b += rfm_oz_digit_bytes(s, QB, QDIG, 128);  // V
   b += rfm_oz_digit_bytes(n, QB, QDIG, 64);   // W2
-  b += 8LL * (2LL * QB * (n + QB) + 3LL * QB * QB);
+  b += 8LL * (2LL * QB * (n + QB) + QB * QB);  // [G, W], W2, T
   b += 8LL * 8 * QB * (n + QB);  // split-K partials of V^T [V, A_t]
   b += 4LL * (QB + n + QB + s + n) + 4096;
   return b;
@@ -718,7 +718,6 @@ rfm_status rfm_householder_emulated(double* A, long long s, long long n, long lo
   double* T = reinterpret_cast<double*>(take(8LL * QB * QB));
   const long long part_elems = 8LL * QB * (n + QB);
   double* part = reinterpret_cast<double*>(take(8LL * part_elems));
-  (void)take(8LL * QB * QB);
   int* e_vt = reinterpret_cast<int*>(take(4LL * QB));
   int* e_at = reinterpret_cast<int*>(take(4LL * (n + QB)));
   int* e_v = reinterpret_cast<int*>(take(4LL * s));
